@@ -1,0 +1,201 @@
+/*
+ * chns.h -- C ABI of the GB300 (sm_103a) matrix-free CHNS operator library.
+ *
+ * The library applies the fully discrete Crank-Nicolson, residual-based VMS
+ * weak form of the Cahn-Hilliard-Navier-Stokes system (Sec. 3.1 time scheme,
+ * Definition of the fully discrete VMS problem in Sec. 3.4) on trilinear
+ * (bilinear in 2D) continuous Galerkin elements over the leaves of a 2:1
+ * balanced octree (quadtree), with hanging nodes interpolated before and
+ * eliminated after each element operation (Sec. 4, "Handling hanging nodes"),
+ * and advances one time step by Newton's method (Sec. 3.5).
+ *
+ * Unknowns.  Every independent (non-hanging) mesh node carries dim+3 values,
+ * interleaved per node in the order [v_1 .. v_dim, p, phi, mu]; a state
+ * vector has n_dof = n_nodes * (dim+3) entries.  The library numbers nodes
+ * itself; chns_mesh_node_coords returns their integer coordinates so callers
+ * can map their data.
+ *
+ * Memory.  Meshes and batches are opaque, library-owned objects holding device
+ * arrays and the solver's scratch.  Every state vector passed to the calls
+ * below is a DEVICE pointer owned by the caller (n_dof entries, 16-byte
+ * aligned), unless the comment says "host".  Calls are asynchronous on the
+ * given CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) except where they return host values; those synchronise the stream.
+ *
+ * Errors.  Every call returns a chns_status; on failure chns_last_error()
+ * gives a message (thread-local, valid until the next call on that thread).
+ * No call traps or aborts the process; kernels never spin without a bound.
+ *
+ * Boundary conditions (Sec. 3.1): no-slip walls on every face of the box
+ * (velocity rows of wall nodes are replaced by v - g), zero normal flux of
+ * phi and mu (natural), and the pressure pinned at the node at the box
+ * origin (its continuity row is replaced by p - g).
+ */
+#ifndef CHNS_H
+#define CHNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chns_mesh chns_mesh;
+typedef struct chns_batch chns_batch;
+
+typedef enum {
+  CHNS_OK = 0,
+  CHNS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad option) */
+  CHNS_ERR_MESH = 2,       /* leaves unsorted, overlapping, or not 2:1 balanced */
+  CHNS_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  CHNS_ERR_NONFINITE = 4,  /* NaN or Inf in a residual or Krylov norm */
+  CHNS_ERR_NEWTON = 5,     /* Newton did not reach its tolerance in newton_max_it */
+  CHNS_ERR_KRYLOV = 6,     /* FGMRES breakdown or no progress */
+  CHNS_ERR_TIMEOUT = 7,    /* a bounded device-side wait ran out */
+  CHNS_ERR_OOM = 8         /* device allocation failed */
+} chns_status;
+
+typedef enum {
+  CHNS_FP64 = 0,           /* everything in double precision */
+  CHNS_FP32_BULK = 1       /* element and Krylov-vector kernels in float, Newton in double */
+} chns_precision;
+
+/* Nondimensional parameters (Sec. 2).  rho_ratio = rho_-/rho_+ and
+ * eta_ratio = eta_-/eta_+ (fluid "+" at phi = +1 is the reference, rho = eta = 1).
+ * gravity is the unit vector g^ (the paper's default is (0,-1,0)); C_I is the
+ * constant of tau_m (6 in the paper). */
+typedef struct {
+  int dim;
+  double dt, Cn, Re, We, Pe, Fr, rho_ratio, eta_ratio, C_I;
+  double gravity[3];
+} chns_params;
+
+typedef struct {
+  double newton_rtol;      /* stop when ||F||_2 <= newton_rtol ||F(initial guess)||_2 ... */
+  double newton_atol;      /* ... or ||F||_2 <= newton_atol */
+  int newton_max_it;
+  double krylov_rtol;      /* FGMRES relative tolerance of each Newton correction */
+  int krylov_restart;      /* FGMRES restart length m (1..64) */
+  int krylov_max_it;       /* total FGMRES iterations per Newton correction */
+  chns_precision precision;
+  int reuse_preconditioner;/* 1: block-Jacobi built once per step; 0: every Newton iteration */
+} chns_solver_opts;
+
+typedef struct {
+  int newton_its;
+  int krylov_its_total;
+  double res0, res_final;          /* ||F|| at the initial guess and at exit */
+  double energy_old, energy_new;   /* energy functional of U_n and U_{n+1} */
+  double mass_old, mass_new;       /* integral of phi */
+  double seconds;                  /* host wall time of the call */
+  double jacvec_ms;                /* device time of the Krylov J.w applies (CUDA events) */
+  int jacvec_calls;
+  double residual_ms;              /* device time of the FP64 residual applies */
+  int residual_calls;
+  double precond_ms;               /* device time of building the block-Jacobi preconditioner */
+} chns_step_stats;
+
+/* ---------------------------------------------------------------- meshes */
+
+/* Build a mesh from the leaves of a linear octree (dim = 3) or quadtree
+ * (dim = 2) given in Morton order (Sec. 4 "Meshing").  Host arrays:
+ * level[n_leaves] (0..max_level) and anchor[n_leaves*dim] (integer lower
+ * corner of each leaf at max_level resolution, x fastest).  The domain is the
+ * box [lo, hi].  The leaves must tile the box, be sorted by Morton key, and
+ * be 2:1 balanced across faces, edges and corners (Sec. 4 "2:1 Balancing");
+ * otherwise CHNS_ERR_MESH.  Colours the elements so that elements of one
+ * colour touch disjoint node sets (hanging constraints included), which
+ * makes the scatter-add free of atomics and deterministic. */
+chns_status chns_mesh_create(int dim, int64_t n_leaves, const uint8_t *level,
+                             const uint32_t *anchor, int max_level, const double lo[3],
+                             const double hi[3], chns_mesh **out);
+
+/* Host outputs; any pointer may be NULL. */
+chns_status chns_mesh_info(const chns_mesh *mesh, int64_t *n_nodes, int64_t *n_dof,
+                           int *n_colours, int64_t *n_hanging);
+
+/* Integer coordinates (max_level resolution) of the independent nodes in the
+ * library's numbering.  Host output xyz[n_nodes*dim]. */
+chns_status chns_mesh_node_coords(const chns_mesh *mesh, int64_t *xyz);
+
+void chns_mesh_destroy(chns_mesh *mesh);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Nonlinear residual F(U_new; U_old) of the fully discrete CN-VMS problem
+ * (Sec. 3.4 Definition with the time derivative replaced by the CN scheme of
+ * Sec. 3.1), in double precision.  forcing (nullable): nodal source at
+ * t_{k+1/2}, subtracted from every row and inside the strong residuals.
+ * bc (nullable, 0 if NULL): prescribed values of the constrained rows (wall
+ * velocities at t_{k+1}, pinned pressure); other entries are ignored.
+ * F is overwritten. */
+chns_status chns_residual(const chns_mesh *mesh, const chns_params *params,
+                          const double *U_new, const double *U_old, const double *forcing,
+                          const double *bc, double *F, void *stream);
+
+/* Jacobian-vector product y = (dF/dU_new)(U_new; U_old) w (Sec. 3.5: the
+ * analytic Jacobian), exact directional derivative including tau_m, tau_c,
+ * the phi* clip and rho(phi^{k+1}).  prec = CHNS_FP64: w, y are double*.
+ * prec = CHNS_FP32_BULK: w, y are float* and the element arithmetic is
+ * float (the states are rounded to float after forming their CN averages
+ * and increments in double).  Constrained rows give y = w. */
+chns_status chns_jacvec(const chns_mesh *mesh, const chns_params *params,
+                        const double *U_new, const double *U_old, const void *w, void *y,
+                        chns_precision prec, void *stream);
+
+/* Replace the chemical potential of U (in place) by the L2 projection of
+ * psi'(phi) - Cn^2 lap(phi), i.e. solve M mu = (N, psi'(phi)) + Cn^2 (grad N,
+ * grad phi) (the chemical-potential row with U_new = U_old). */
+chns_status chns_init_mu(const chns_mesh *mesh, const chns_params *params, double *U,
+                         void *stream);
+
+/* One Crank-Nicolson step (Sec. 3.1, 3.5): Newton on F(U; U_n) = 0 from the
+ * guess U_n (or 2 U_n - U_nm1 when U_nm1 is not NULL), each correction by
+ * right-preconditioned FGMRES(m) with nodal block-Jacobi.  The residual and
+ * the Newton update are double; with CHNS_FP32_BULK the Krylov J.w and
+ * preconditioner run in float and the Gram-Schmidt inner products and norms
+ * stay double (iterative refinement by the outer double residual).  U_np1
+ * receives the result (may not alias U_n).  stats (host, nullable). */
+chns_status chns_step(const chns_mesh *mesh, const chns_params *params,
+                      const chns_solver_opts *opts, const double *U_n, const double *U_nm1,
+                      const double *forcing, const double *bc, double *U_np1,
+                      chns_step_stats *stats, void *stream);
+
+/* Diagnostics with the same 2^dim Gauss rule (host outputs, synchronises):
+ * energy functional (Eq. energy_functional, gravity potential (1/Fr) rho(phi*)
+ * (-g.x)), integral of phi (Prop. mass_conservation) and the volume where
+ * phi < 0 (the bubble mass of Sec. 5.2).  Any output pointer may be NULL. */
+chns_status chns_energy_mass(const chns_mesh *mesh, const chns_params *params,
+                             const double *U, double *energy, double *mass,
+                             double *bubble_mass, void *stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent problems (meshes of any size, own parameters) advanced
+ * together: the element kernels run over the concatenated leaves of all
+ * instances in one launch per colour.  meshes and params: host arrays of n
+ * entries; the meshes must outlive the batch. */
+chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params *params,
+                              chns_batch **out);
+
+/* One CN step of every instance; U_n[i], U_nm1[i] (nullable array or
+ * entries), U_np1[i] are device vectors of instance i.  stats: host array of
+ * n entries or NULL. */
+chns_status chns_batch_step(chns_batch *batch, const chns_solver_opts *opts,
+                            double *const *U_n, double *const *U_nm1, double *const *U_np1,
+                            chns_step_stats *stats, void *stream);
+
+void chns_batch_destroy(chns_batch *batch);
+
+const char *chns_last_error(void);
+
+/* Tracing: number of kernels this library has launched in this process so
+ * far (all devices, all streams).  Read it before and after a region to count
+ * the region's launches. */
+uint64_t chns_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHNS_H */

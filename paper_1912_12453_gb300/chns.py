@@ -1,0 +1,261 @@
+"""Python binding of libchns (ctypes): argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``libchns.so``; this module
+passes torch CUDA tensors' device pointers and the current CUDA stream.  If
+the library is not built, ``lib()`` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchns.so")
+
+CHNS_FP64 = 0
+CHNS_FP32_BULK = 1
+STATUS = {0: "CHNS_OK", 1: "CHNS_ERR_ARG", 2: "CHNS_ERR_MESH", 3: "CHNS_ERR_CUDA",
+          4: "CHNS_ERR_NONFINITE", 5: "CHNS_ERR_NEWTON", 6: "CHNS_ERR_KRYLOV",
+          7: "CHNS_ERR_TIMEOUT", 8: "CHNS_ERR_OOM"}
+
+EXPORTS = ["chns_mesh_create", "chns_mesh_info", "chns_mesh_node_coords", "chns_mesh_destroy",
+           "chns_residual", "chns_jacvec", "chns_init_mu", "chns_step", "chns_energy_mass",
+           "chns_batch_create", "chns_batch_step", "chns_batch_destroy", "chns_last_error",
+           "chns_kernel_launches"]
+
+
+class ChnsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("dt", ctypes.c_double), ("Cn", ctypes.c_double),
+                ("Re", ctypes.c_double), ("We", ctypes.c_double), ("Pe", ctypes.c_double),
+                ("Fr", ctypes.c_double), ("rho_ratio", ctypes.c_double), ("eta_ratio", ctypes.c_double),
+                ("C_I", ctypes.c_double), ("gravity", ctypes.c_double * 3)]
+
+    @classmethod
+    def of(cls, p) -> "Params":
+        """From any object with the fields of workloads.Params."""
+        return cls(int(p.dim), p.dt, p.Cn, p.Re, p.We, p.Pe, p.Fr, p.rho_ratio, p.eta_ratio, p.C_I,
+                   (ctypes.c_double * 3)(*p.gravity))
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
+                ("newton_max_it", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
+                ("krylov_restart", ctypes.c_int), ("krylov_max_it", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reuse_preconditioner", ctypes.c_int)]
+
+    @classmethod
+    def make(cls, precision="fp64", newton_rtol=1e-10, newton_atol=1e-13, newton_max_it=20,
+             krylov_rtol=1e-4, krylov_restart=30, krylov_max_it=600, reuse_preconditioner=True):
+        prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
+        return cls(newton_rtol, newton_atol, newton_max_it, krylov_rtol, krylov_restart, krylov_max_it,
+                   prec, int(bool(reuse_preconditioner)))
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("krylov_its_total", ctypes.c_int),
+                ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("energy_old", ctypes.c_double), ("energy_new", ctypes.c_double),
+                ("mass_old", ctypes.c_double), ("mass_new", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("jacvec_ms", ctypes.c_double),
+                ("jacvec_calls", ctypes.c_int), ("residual_ms", ctypes.c_double),
+                ("residual_calls", ctypes.c_int), ("precond_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libchns.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int
+        L.chns_last_error.restype = ctypes.c_char_p
+        L.chns_kernel_launches.restype = ctypes.c_uint64
+        L.chns_kernel_launches.argtypes = []
+        L.chns_mesh_create.restype = st
+        L.chns_mesh_create.argtypes = [i32, i64, vp, vp, i32, vp, vp, ctypes.POINTER(vp)]
+        L.chns_mesh_info.restype = st
+        L.chns_mesh_info.argtypes = [vp, vp, vp, vp, vp]
+        L.chns_mesh_node_coords.restype = st
+        L.chns_mesh_node_coords.argtypes = [vp, vp]
+        L.chns_mesh_destroy.argtypes = [vp]
+        L.chns_mesh_destroy.restype = None
+        L.chns_residual.restype = st
+        L.chns_residual.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.chns_jacvec.restype = st
+        L.chns_jacvec.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+        L.chns_init_mu.restype = st
+        L.chns_init_mu.argtypes = [vp, vp, vp, vp]
+        L.chns_step.restype = st
+        L.chns_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.chns_energy_mass.restype = st
+        L.chns_energy_mass.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.chns_batch_create.restype = st
+        L.chns_batch_create.argtypes = [i32, vp, vp, ctypes.POINTER(vp)]
+        L.chns_batch_step.restype = st
+        L.chns_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.chns_batch_destroy.argtypes = [vp]
+        L.chns_batch_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise ChnsError(status, lib().chns_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+class Mesh:
+    """A library-owned mesh built from octree leaves (host arrays)."""
+
+    def __init__(self, leaves, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+        L = lib()
+        self.dim = int(leaves.dim)
+        self.max_level = int(leaves.max_level)
+        self.nf = self.dim + 3
+        lev = np.ascontiguousarray(leaves.level, dtype=np.uint8)
+        anc = np.ascontiguousarray(leaves.anchor, dtype=np.uint32)
+        self._lo = (ctypes.c_double * 3)(*lo)
+        self._hi = (ctypes.c_double * 3)(*hi)
+        h = ctypes.c_void_p()
+        _check(L.chns_mesh_create(self.dim, lev.shape[0], lev.ctypes.data, anc.ctypes.data, self.max_level,
+                                  ctypes.addressof(self._lo), ctypes.addressof(self._hi), ctypes.byref(h)))
+        self._h = h
+        nn, nd, nh = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        nc = ctypes.c_int()
+        _check(L.chns_mesh_info(h, ctypes.byref(nn), ctypes.byref(nd), ctypes.byref(nc), ctypes.byref(nh)))
+        self.n_nodes, self.n_dof, self.n_colours, self.n_hanging = nn.value, nd.value, nc.value, nh.value
+        self.n_elem = int(lev.shape[0])
+        self.coords_int = np.zeros((self.n_nodes, self.dim), dtype=np.int64)
+        _check(L.chns_mesh_node_coords(h, self.coords_int.ctypes.data))
+        lo_a = np.asarray(lo[: self.dim], dtype=np.float64)
+        hi_a = np.asarray(hi[: self.dim], dtype=np.float64)
+        self.coords = lo_a + self.coords_int * ((hi_a - lo_a) / float(1 << self.max_level))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.chns_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def residual(mesh: Mesh, params, U_new, U_old, forcing=None, bc=None, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(U_new)
+    prm = Params.of(params)
+    _check(lib().chns_residual(mesh.handle, ctypes.byref(prm), _ptr(U_new), _ptr(U_old), _ptr(forcing),
+                               _ptr(bc), _ptr(out), _stream(stream)))
+    return out
+
+
+def jacvec(mesh: Mesh, params, U_new, U_old, w, out=None, precision="fp64", stream=None):
+    import torch
+    prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
+    want = torch.float64 if prec == CHNS_FP64 else torch.float32
+    if w.dtype != want:
+        raise ValueError(f"w must be {want} for precision {precision}")
+    if out is None:
+        out = torch.empty_like(w)
+    prm = Params.of(params)
+    _check(lib().chns_jacvec(mesh.handle, ctypes.byref(prm), _ptr(U_new), _ptr(U_old), _ptr(w), _ptr(out),
+                             prec, _stream(stream)))
+    return out
+
+
+def init_mu(mesh: Mesh, params, U, stream=None):
+    prm = Params.of(params)
+    _check(lib().chns_init_mu(mesh.handle, ctypes.byref(prm), _ptr(U), _stream(stream)))
+    return U
+
+
+def step(mesh: Mesh, params, U_n, out, opts: Optional[SolverOpts] = None, U_nm1=None, forcing=None, bc=None,
+         stream=None, stats=True):
+    prm = Params.of(params)
+    o = opts or SolverOpts.make()
+    s = StepStats() if stats else None
+    _check(lib().chns_step(mesh.handle, ctypes.byref(prm), ctypes.byref(o), _ptr(U_n), _ptr(U_nm1),
+                           _ptr(forcing), _ptr(bc), _ptr(out), ctypes.byref(s) if s is not None else None,
+                           _stream(stream)))
+    return s.as_dict() if s is not None else None
+
+
+def energy_mass(mesh: Mesh, params, U, stream=None):
+    prm = Params.of(params)
+    e, m, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().chns_energy_mass(mesh.handle, ctypes.byref(prm), _ptr(U), ctypes.byref(e), ctypes.byref(m),
+                                  ctypes.byref(b), _stream(stream)))
+    return e.value, m.value, b.value
+
+
+def kernel_launches() -> int:
+    return int(lib().chns_kernel_launches())
+
+
+class Batch:
+    def __init__(self, meshes: Sequence[Mesh], params: Sequence):
+        self.meshes = list(meshes)
+        n = len(self.meshes)
+        arr = (ctypes.c_void_p * n)(*[m.handle.value for m in self.meshes])
+        prm = (Params * n)(*[Params.of(p) for p in params])
+        h = ctypes.c_void_p()
+        _check(lib().chns_batch_create(n, arr, prm, ctypes.byref(h)))
+        self._h = h
+
+    def step(self, U_n, out, opts: Optional[SolverOpts] = None, U_nm1=None, stream=None):
+        n = len(self.meshes)
+        o = opts or SolverOpts.make()
+        a = (ctypes.c_void_p * n)(*[_ptr(u) for u in U_n])
+        c = (ctypes.c_void_p * n)(*[_ptr(u) for u in out])
+        b = (ctypes.c_void_p * n)(*[_ptr(u) for u in U_nm1]) if U_nm1 is not None else None
+        st = (StepStats * n)()
+        _check(lib().chns_batch_step(self._h, ctypes.byref(o), a, b, c, st, _stream(stream)))
+        return [s.as_dict() for s in st]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.chns_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,619 @@
+// C ABI of libchns: meshes, operator applies, the Newton-Krylov CN step
+// (Sec. 3.5), diagnostics and batches.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "chns_internal.h"
+#include "kernels.h"
+#include "vector.h"
+
+namespace chns {
+chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor, int max_level,
+                       const double lo[3], const double hi[3], chns_mesh *m);
+const char *last_error();
+uint64_t launches();
+}  // namespace chns
+
+using namespace chns;
+
+namespace {
+
+inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+#define TRY(expr)                               \
+  do {                                          \
+    chns_status s_ = (expr);                    \
+    if (s_ != CHNS_OK) return s_;               \
+  } while (0)
+
+chns_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("kernel launch failed: %s", cudaGetErrorString(e));
+    return CHNS_ERR_CUDA;
+  }
+  return CHNS_OK;
+}
+
+chns_status check_params(const chns_mesh *m, const chns_params *p) {
+  if (!m || !p) { set_error("null mesh or params"); return CHNS_ERR_ARG; }
+  if (p->dim != m->dim) { set_error("params.dim %d != mesh dim %d", p->dim, m->dim); return CHNS_ERR_ARG; }
+  if (!(p->dt > 0) || !(p->Cn > 0) || !(p->Re > 0) || !(p->We > 0) || !(p->Pe > 0) || !(p->Fr > 0) ||
+      !(p->rho_ratio > 0) || !(p->eta_ratio > 0) || !(p->C_I >= 0)) {
+    set_error("parameters must be positive");
+    return CHNS_ERR_ARG;
+  }
+  return CHNS_OK;
+}
+
+// prepared nodal fields (CN averages and increments) in precision T
+template <typename T>
+chns_status prepare(chns_mesh *m, const double *Un, const double *Uo, cudaStream_t st, T **ut, T **dl) {
+  Workspace &ws = m->ws;
+  DevBuf &bu = sizeof(T) == 8 ? ws.ut : ws.ut32;
+  DevBuf &bd = sizeof(T) == 8 ? ws.dl : ws.dl32;
+  TRY(bu.ensure(sizeof(T) * m->n_nodes * m->nf));
+  TRY(bd.ensure(sizeof(T) * m->n_nodes * (m->dim + 1)));
+  launch_prep<T>(m, Un, Uo, bu.as<T>(), bd.as<T>(), st);
+  *ut = bu.as<T>();
+  *dl = bd.as<T>();
+  return check_launch();
+}
+
+chns_status residual_prepared(chns_mesh *m, const PhysCoef &pc, const double *Un, const double *ut,
+                              const double *dl, const double *forcing, const double *bc, double *F,
+                              cudaStream_t st) {
+  CHNS_CUDA_TRY(cudaMemsetAsync(F, 0, sizeof(double) * m->n_nodes * m->nf, st));
+  launch_residual(m, pc, ut, dl, forcing, F, st);
+  launch_dirichlet_res(m, Un, bc, F, st);
+  return check_launch();
+}
+
+template <typename T>
+chns_status jacvec_prepared(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *y,
+                            cudaStream_t st) {
+  CHNS_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(T) * m->n_nodes * m->nf, st));
+  launch_jacvec<T>(m, pc, ut, dl, w, y, st);
+  launch_dirichlet_jv<T>(m, w, y, st);
+  return check_launch();
+}
+
+chns_status ensure_events(Workspace &ws, size_t n) {
+  while (ws.ev.size() < n) {
+    cudaEvent_t e;
+    CHNS_CUDA_TRY(cudaEventCreate(&e));
+    ws.ev.push_back(e);
+  }
+  return CHNS_OK;
+}
+
+chns_status ensure_pinned(Workspace &ws) {
+  if (!ws.hpinned) CHNS_CUDA_TRY(cudaMallocHost(&ws.hpinned, sizeof(double) * 4 * (kMaxRestart + 8)));
+  return CHNS_OK;
+}
+
+chns_status norm2(chns_mesh *m, const double *x, double *out_host, cudaStream_t st) {
+  Workspace &ws = m->ws;
+  int64_t n = m->n_nodes * m->nf;
+  TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+  TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+  TRY(ensure_pinned(ws));
+  double *hd = ws.hdev.as<double>();
+  vec_dot(x, x, n, ws.red.as<double>(), hd, st);
+  CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, hd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  *out_host = std::sqrt(ws.hpinned[0]);
+  return CHNS_OK;
+}
+
+// Per-call timing of a group of launches with CUDA events on the stream.
+struct Timer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double ms = 0.0;
+  int calls = 0;
+  size_t next = 0;
+  Workspace *ws = nullptr;
+  bool on = false;
+  chns_status begin(cudaStream_t st, cudaEvent_t *a) {
+    if (!on) return CHNS_OK;
+    TRY(ensure_events(*ws, next + 2));
+    *a = ws->ev[next];
+    CHNS_CUDA_TRY(cudaEventRecord(*a, st));
+    return CHNS_OK;
+  }
+  chns_status end(cudaStream_t st, cudaEvent_t a) {
+    if (!on) return CHNS_OK;
+    cudaEvent_t b = ws->ev[next + 1];
+    CHNS_CUDA_TRY(cudaEventRecord(b, st));
+    pending.push_back({a, b});
+    next += 2;
+    return CHNS_OK;
+  }
+  // after a stream synchronisation
+  chns_status collect() {
+    for (auto &p : pending) {
+      float t = 0.f;
+      CHNS_CUDA_TRY(cudaEventElapsedTime(&t, p.first, p.second));
+      ms += t;
+      ++calls;
+    }
+    pending.clear();
+    next = 0;
+    return CHNS_OK;
+  }
+};
+
+// ---------------------------------------------------------------- block-Jacobi by probing
+// The nodal (nf x nf) diagonal blocks of J are read off J applied to the
+// indicator of one field on the nodes of one node colour: nodes of a colour
+// never share an element, so each probed node sees only its own block.
+template <typename T>
+chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, cudaStream_t st) {
+  Workspace &ws = m->ws;
+  const int nf = m->nf;
+  const int64_t n = m->n_nodes * nf;
+  TRY(ws.binv.ensure(sizeof(T) * m->n_nodes * nf * nf + 16));
+  TRY(ws.wv.ensure(sizeof(T) * n));
+  TRY(ws.yv.ensure(sizeof(T) * n));
+  T *w = ws.wv.as<T>(), *y = ws.yv.as<T>(), *B = ws.binv.as<T>();
+  for (int c = 0; c < m->n_node_colours; ++c) {
+    int64_t b = m->node_colour_start[c], e = m->node_colour_start[c + 1];
+    for (int f = 0; f < nf; ++f) {
+      CHNS_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(T) * n, st));
+      probe_set<T>(m->node_perm + b, e - b, nf, f, w, st);
+      TRY(jacvec_prepared<T>(m, pc, ut, dl, w, y, st));
+      probe_get<T>(m->node_perm + b, e - b, nf, f, y, B, st);
+    }
+  }
+  int *bad = reinterpret_cast<int *>(reinterpret_cast<char *>(B) + sizeof(T) * m->n_nodes * nf * nf);
+  CHNS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  invert_blocks<T>(B, m->n_nodes, nf, bad, st);
+  int hbad = 0;
+  CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hbad) { set_error("singular nodal diagonal block in the preconditioner"); return CHNS_ERR_KRYLOV; }
+  return check_launch();
+}
+
+// ---------------------------------------------------------------- FGMRES
+// Solve J x = b (b = -F) with right-preconditioned flexible GMRES(m); Gram-
+// Schmidt (classical, applied twice), norms and the basis V in double; the
+// preconditioned directions Z and J.z in precision T.
+template <typename T>
+chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const double *b, double *x,
+                   const chns_solver_opts &o, int *its_out, Timer &tj, cudaStream_t st) {
+  Workspace &ws = m->ws;
+  const int nf = m->nf;
+  const int64_t n = m->n_nodes * nf;
+  const int mr = o.krylov_restart;
+  TRY(ws.V.ensure(sizeof(double) * (mr + 1) * n));
+  TRY(ws.Z.ensure(sizeof(T) * mr * n));
+  TRY(ws.r.ensure(sizeof(double) * n));
+  TRY(ws.wv.ensure(sizeof(T) * n));
+  TRY(ws.yv.ensure(sizeof(T) * n));
+  TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+  TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+  TRY(ensure_pinned(ws));
+  double *V = ws.V.as<double>(), *r = ws.r.as<double>();
+  T *Z = ws.Z.as<T>(), *yv = ws.yv.as<T>(), *tv = ws.wv.as<T>();
+  double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>(), *hp = ws.hpinned;
+  double *h1 = hd, *h2 = hd + (kMaxRestart + 8), *nr = hd + 2 * (kMaxRestart + 8);
+  double *cz = hd + 3 * (kMaxRestart + 8);
+  const T *Binv = ws.binv.as<T>();
+
+  CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  CHNS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double beta0 = 0.0;
+  TRY(norm2(m, r, &beta0, st));
+  if (!std::isfinite(beta0)) { set_error("non-finite right-hand side"); return CHNS_ERR_NONFINITE; }
+  *its_out = 0;
+  if (beta0 == 0.0) return CHNS_OK;
+  const double target = o.krylov_rtol * beta0;
+  double beta = beta0;
+  std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), yk(mr);
+  int total = 0;
+  while (true) {
+    // V_0 = r / beta
+    vec_axpby(1.0 / beta, r, 0.0, V, n, st);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_end = 0;
+    bool done = false;
+    for (int j = 0; j < mr; ++j) {
+      double *vj = V + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
+      T *zj = Z + (int64_t)j * n;
+      block_apply<T>(Binv, vj, zj, m->n_nodes, nf, st);
+      cudaEvent_t e0 = nullptr;
+      TRY(tj.begin(st, &e0));
+      TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, yv, st));
+      TRY(tj.end(st, e0));
+      vec_convert<T, double>(yv, w, n, 1.0, st);
+      // classical Gram-Schmidt, twice
+      vec_multidot(V, n, j + 1, w, n, part, h1, st);
+      vec_update(V, n, j + 1, h1, w, n, st);
+      vec_multidot(V, n, j + 1, w, n, part, h2, st);
+      vec_update(V, n, j + 1, h2, w, n, st);
+      vec_dot(w, w, n, part, nr, st);
+      CHNS_CUDA_TRY(cudaMemcpyAsync(hp, hd, sizeof(double) * 3 * (kMaxRestart + 8), cudaMemcpyDeviceToHost, st));
+      CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+      TRY(tj.collect());
+      double hn = std::sqrt(hp[2 * (kMaxRestart + 8)]);
+      if (!std::isfinite(hn)) { set_error("non-finite Krylov vector"); return CHNS_ERR_NONFINITE; }
+      for (int i = 0; i <= j; ++i) H[i * mr + j] = hp[i] + hp[(kMaxRestart + 8) + i];
+      H[(j + 1) * mr + j] = hn;
+      if (hn > 0.0) {
+        // V_{j+1} = w / hn  (reads the device copy of ||w||^2)
+        vec_axpby(1.0 / hn, w, 0.0, w, n, st);
+      }
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * mr + j], c = H[(i + 1) * mr + j];
+        H[i * mr + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * mr + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[j * mr + j], c = H[(j + 1) * mr + j];
+      double rr = std::hypot(a, c);
+      if (rr == 0.0) { set_error("FGMRES breakdown"); return CHNS_ERR_KRYLOV; }
+      cs[j] = a / rr;
+      sn[j] = c / rr;
+      H[j * mr + j] = rr;
+      H[(j + 1) * mr + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      j_end = j + 1;
+      if (std::fabs(g[j + 1]) <= target || hn == 0.0) { done = true; break; }
+      if (total >= o.krylov_max_it) break;
+    }
+    // y = H^{-1} g, x += Z y
+    for (int i = j_end - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j_end; ++k) s -= H[i * mr + k] * yk[k];
+      yk[i] = s / H[i * mr + i];
+    }
+    CHNS_CUDA_TRY(cudaMemcpyAsync(cz, yk.data(), sizeof(double) * j_end, cudaMemcpyHostToDevice, st));
+    vec_combine<T>(Z, n, j_end, cz, x, n, st);
+    if (done || total >= o.krylov_max_it) break;
+    // restart: r = b - J x
+    vec_convert<double, T>(x, tv, n, 1.0, st);
+    cudaEvent_t e0 = nullptr;
+    TRY(tj.begin(st, &e0));
+    TRY(jacvec_prepared<T>(m, pc, ut, dl, tv, yv, st));
+    TRY(tj.end(st, e0));
+    vec_convert<T, double>(yv, r, n, 1.0, st);
+    vec_lincomb(1.0, b, -1.0, r, r, n, st);
+    TRY(norm2(m, r, &beta, st));
+    TRY(tj.collect());
+    if (!std::isfinite(beta)) { set_error("non-finite Krylov residual"); return CHNS_ERR_NONFINITE; }
+    if (beta <= target) break;
+  }
+  *its_out = total;
+  return check_launch();
+}
+
+template <typename T>
+chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_opts &o, const double *Un,
+                        const double *Unm1, const double *forcing, const double *bc, double *U,
+                        chns_step_stats *stats, cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  Workspace &ws = m->ws;
+  const int64_t n = m->n_nodes * m->nf;
+  PhysCoef pc = make_coef(*p, m->lo, m->hi);
+  TRY(ws.F.ensure(sizeof(double) * n));
+  TRY(ws.dU.ensure(sizeof(double) * n));
+  double *F = ws.F.as<double>(), *dU = ws.dU.as<double>();
+  Timer tj, tr, tp;  // accumulated J.w, residual and preconditioner times
+
+  if (Unm1) vec_lincomb(2.0, Un, -1.0, Unm1, U, n, st);
+  else CHNS_CUDA_TRY(cudaMemcpyAsync(U, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+
+  double *ut = nullptr, *dl = nullptr;
+  auto residual = [&](double *fn) -> chns_status {
+    TRY(prepare<double>(m, U, Un, st, &ut, &dl));
+    cudaEvent_t e0 = nullptr;
+    if (stats) { TRY(ensure_events(ws, 64)); e0 = ws.ev[60]; CHNS_CUDA_TRY(cudaEventRecord(e0, st)); }
+    TRY(residual_prepared(m, pc, U, ut, dl, forcing, bc, F, st));
+    if (stats) CHNS_CUDA_TRY(cudaEventRecord(ws.ev[61], st));
+    TRY(norm2(m, F, fn, st));
+    if (stats) {
+      float t = 0.f;
+      CHNS_CUDA_TRY(cudaEventElapsedTime(&t, ws.ev[60], ws.ev[61]));
+      tr.ms += t;
+      tr.calls++;
+    }
+    if (!std::isfinite(*fn)) { set_error("non-finite residual norm"); return CHNS_ERR_NONFINITE; }
+    return CHNS_OK;
+  };
+  double fn = 0.0;
+  TRY(residual(&fn));
+  const double f0 = fn;
+  int its = 0, kits = 0;
+  bool have_pc = false;
+  while (!(fn <= std::max(o.newton_rtol * f0, o.newton_atol))) {
+    if (its >= o.newton_max_it) {
+      set_error("Newton reached %d iterations with ||F|| = %.3e (start %.3e)", its, fn, f0);
+      if (stats) { stats->newton_its = its; stats->res_final = fn; }
+      return CHNS_ERR_NEWTON;
+    }
+    T *ut_t = nullptr, *dl_t = nullptr;
+    TRY(prepare<T>(m, U, Un, st, &ut_t, &dl_t));
+    if (!have_pc || !o.reuse_preconditioner) {
+      auto a = std::chrono::steady_clock::now();
+      TRY(build_block_jacobi<T>(m, pc, ut_t, dl_t, st));
+      tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+      have_pc = true;
+    }
+    vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
+    int k = 0;
+    Timer tk;  // event slots 0.. (the residual uses slots 60, 61)
+    tk.ws = &ws;
+    tk.on = stats != nullptr;
+    TRY(fgmres<T>(m, pc, ut_t, dl_t, F, dU, o, &k, tk, st));
+    tj.ms += tk.ms;
+    tj.calls += tk.calls;
+    kits += k;
+    vec_axpby(1.0, dU, 1.0, U, n, st);
+    ++its;
+    TRY(residual(&fn));
+  }
+  if (stats) {
+    stats->newton_its = its;
+    stats->krylov_its_total = kits;
+    stats->res0 = f0;
+    stats->res_final = fn;
+    stats->jacvec_ms = tj.ms;
+    stats->jacvec_calls = tj.calls;
+    stats->residual_ms = tr.ms;
+    stats->residual_calls = tr.calls;
+    stats->precond_ms = tp.ms;
+  }
+  (void)t0;
+  return CHNS_OK;
+}
+
+chns_status step_impl(chns_mesh *m, const chns_params *p, const chns_solver_opts *o, const double *U_n,
+                      const double *U_nm1, const double *forcing, const double *bc, double *U_np1,
+                      chns_step_stats *stats, cudaStream_t st);
+
+chns_status energy_mass_impl(chns_mesh *m, const chns_params *p, const double *U, double out[3],
+                             cudaStream_t st) {
+  PhysCoef pc = make_coef(*p, m->lo, m->hi);
+  int64_t nb = energy_blocks(m);
+  TRY(m->ws.red.ensure(sizeof(double) * std::max<int64_t>(3 * nb, (kMaxRestart + 16) * red_blocks())));
+  launch_energy(m, pc, U, m->ws.red.as<double>(), st);
+  TRY(check_launch());
+  std::vector<double> h(3 * nb);
+  CHNS_CUDA_TRY(cudaMemcpyAsync(h.data(), m->ws.red.as<double>(), sizeof(double) * 3 * nb,
+                                cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  out[0] = out[1] = out[2] = 0.0;
+  for (int64_t b = 0; b < nb; ++b)
+    for (int k = 0; k < 3; ++k) out[k] += h[b * 3 + k];
+  return CHNS_OK;
+}
+
+chns_status step_impl(chns_mesh *m, const chns_params *p, const chns_solver_opts *o, const double *U_n,
+                      const double *U_nm1, const double *forcing, const double *bc, double *U_np1,
+                      chns_step_stats *stats, cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!o || !U_n || !U_np1) { set_error("null argument"); return CHNS_ERR_ARG; }
+  if (U_np1 == U_n) { set_error("U_np1 may not alias U_n"); return CHNS_ERR_ARG; }
+  if (o->krylov_restart < 1 || o->krylov_restart > kMaxRestart || o->krylov_max_it < 1 || o->newton_max_it < 0) {
+    set_error("invalid solver options");
+    return CHNS_ERR_ARG;
+  }
+  chns_status s;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    double em[3];
+    TRY(energy_mass_impl(m, p, U_n, em, st));
+    stats->energy_old = em[0];
+    stats->mass_old = em[1];
+  }
+  if (o->precision == CHNS_FP64)
+    s = newton_step<double>(m, p, *o, U_n, U_nm1, forcing, bc, U_np1, stats, st);
+  else if (o->precision == CHNS_FP32_BULK)
+    s = newton_step<float>(m, p, *o, U_n, U_nm1, forcing, bc, U_np1, stats, st);
+  else {
+    set_error("unknown precision");
+    return CHNS_ERR_ARG;
+  }
+  if (s != CHNS_OK) return s;
+  if (stats) {
+    double em[3];
+    TRY(energy_mass_impl(m, p, U_np1, em, st));
+    stats->energy_new = em[0];
+    stats->mass_new = em[1];
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return CHNS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *chns_last_error(void) { return chns::last_error(); }
+
+uint64_t chns_kernel_launches(void) { return chns::launches(); }
+
+chns_status chns_mesh_create(int dim, int64_t n_leaves, const uint8_t *level, const uint32_t *anchor,
+                             int max_level, const double lo[3], const double hi[3], chns_mesh **out) {
+  if (!out) { set_error("null output"); return CHNS_ERR_ARG; }
+  *out = nullptr;
+  chns_mesh *m = new chns_mesh;
+  chns_status s = build_mesh(dim, n_leaves, level, anchor, max_level, lo, hi, m);
+  if (s != CHNS_OK) {
+    chns_mesh_destroy(m);
+    return s;
+  }
+  *out = m;
+  return CHNS_OK;
+}
+
+chns_status chns_mesh_info(const chns_mesh *m, int64_t *n_nodes, int64_t *n_dof, int *n_colours,
+                           int64_t *n_hanging) {
+  if (!m) { set_error("null mesh"); return CHNS_ERR_ARG; }
+  if (n_nodes) *n_nodes = m->n_nodes;
+  if (n_dof) *n_dof = m->n_nodes * m->nf;
+  if (n_colours) *n_colours = m->n_colours;
+  if (n_hanging) *n_hanging = m->n_hang;
+  return CHNS_OK;
+}
+
+chns_status chns_mesh_node_coords(const chns_mesh *m, int64_t *xyz) {
+  if (!m || !xyz) { set_error("null argument"); return CHNS_ERR_ARG; }
+  std::memcpy(xyz, m->node_xyz.data(), sizeof(int64_t) * m->node_xyz.size());
+  return CHNS_OK;
+}
+
+void chns_mesh_destroy(chns_mesh *m) {
+  if (!m) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  cudaFree(m->conn);
+  cudaFree(m->level);
+  cudaFree(m->anchor);
+  cudaFree(m->hang);
+  cudaFree(m->wall);
+  cudaFree(m->node_perm);
+  m->ws.ut.release(); m->ws.dl.release(); m->ws.ut32.release(); m->ws.dl32.release(); m->ws.f.release();
+  m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
+  m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.red.release(); m->ws.hdev.release();
+  delete m;
+  cudaSetDevice(prev);
+}
+
+chns_status chns_residual(const chns_mesh *mc, const chns_params *p, const double *U_new, const double *U_old,
+                          const double *forcing, const double *bc, double *F, void *stream) {
+  TRY(check_params(mc, p));
+  if (!U_new || !U_old || !F) { set_error("null vector"); return CHNS_ERR_ARG; }
+  chns_mesh *m = const_cast<chns_mesh *>(mc);
+  cudaStream_t st = S(stream);
+  double *ut = nullptr, *dl = nullptr;
+  TRY(prepare<double>(m, U_new, U_old, st, &ut, &dl));
+  PhysCoef pc = make_coef(*p, m->lo, m->hi);
+  return residual_prepared(m, pc, U_new, ut, dl, forcing, bc, F, st);
+}
+
+chns_status chns_jacvec(const chns_mesh *mc, const chns_params *p, const double *U_new, const double *U_old,
+                        const void *w, void *y, chns_precision prec, void *stream) {
+  TRY(check_params(mc, p));
+  if (!U_new || !U_old || !w || !y) { set_error("null vector"); return CHNS_ERR_ARG; }
+  chns_mesh *m = const_cast<chns_mesh *>(mc);
+  cudaStream_t st = S(stream);
+  PhysCoef pc = make_coef(*p, m->lo, m->hi);
+  if (prec == CHNS_FP64) {
+    double *ut = nullptr, *dl = nullptr;
+    TRY(prepare<double>(m, U_new, U_old, st, &ut, &dl));
+    return jacvec_prepared<double>(m, pc, ut, dl, static_cast<const double *>(w), static_cast<double *>(y), st);
+  } else if (prec == CHNS_FP32_BULK) {
+    float *ut = nullptr, *dl = nullptr;
+    TRY(prepare<float>(m, U_new, U_old, st, &ut, &dl));
+    return jacvec_prepared<float>(m, pc, ut, dl, static_cast<const float *>(w), static_cast<float *>(y), st);
+  }
+  set_error("unknown precision %d", (int)prec);
+  return CHNS_ERR_ARG;
+}
+
+chns_status chns_init_mu(const chns_mesh *mc, const chns_params *p, double *U, void *stream) {
+  TRY(check_params(mc, p));
+  if (!U) { set_error("null vector"); return CHNS_ERR_ARG; }
+  chns_mesh *m = const_cast<chns_mesh *>(mc);
+  cudaStream_t st = S(stream);
+  Workspace &ws = m->ws;
+  const int nf = m->nf, imu = m->dim + 2;
+  const int64_t n = m->n_nodes * nf;
+  PhysCoef pc = make_coef(*p, m->lo, m->hi);
+  // M mu_new = M mu + F_mu(U; U), M = -2 (dF_mu / d mu_new); conjugate gradients
+  TRY(ws.F.ensure(sizeof(double) * n));
+  TRY(ws.dU.ensure(sizeof(double) * n));
+  TRY(ws.r.ensure(sizeof(double) * n));
+  TRY(ws.V.ensure(sizeof(double) * 2 * n));
+  double *r = ws.r.as<double>(), *x = ws.dU.as<double>(), *pv = ws.V.as<double>(), *q = pv + n;
+  double *ut = nullptr, *dl = nullptr;
+  TRY(prepare<double>(m, U, U, st, &ut, &dl));
+  TRY(residual_prepared(m, pc, U, ut, dl, nullptr, nullptr, r, st));
+  vec_mask_field(r, m->n_nodes, nf, imu, 1.0, st);
+  CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  CHNS_CUDA_TRY(cudaMemcpyAsync(pv, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double rr = 0.0;
+  TRY(norm2(m, r, &rr, st));
+  rr *= rr;
+  const double stop = 1e-26 * std::max(rr, 1e-300);
+  for (int it = 0; it < 10000 && rr > stop && rr > 0.0; ++it) {
+    TRY(jacvec_prepared<double>(m, pc, ut, dl, pv, q, st));
+    vec_mask_field(q, m->n_nodes, nf, imu, -2.0, st);
+    double pq = 0.0;
+    TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+    TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+    vec_dot(pv, q, n, ws.red.as<double>(), ws.hdev.as<double>(), st);
+    CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, ws.hdev.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+    pq = ws.hpinned[0];
+    if (!(pq > 0.0)) { set_error("mass matrix not positive in CG"); return CHNS_ERR_KRYLOV; }
+    double a = rr / pq;
+    vec_axpby(a, pv, 1.0, x, n, st);
+    vec_axpby(-a, q, 1.0, r, n, st);
+    double rn = 0.0;
+    TRY(norm2(m, r, &rn, st));
+    double rr2 = rn * rn;
+    vec_axpby(1.0, r, rr2 / rr, pv, n, st);
+    rr = rr2;
+  }
+  vec_axpby(1.0, x, 1.0, U, n, st);
+  return check_launch();
+}
+
+chns_status chns_step(const chns_mesh *mc, const chns_params *p, const chns_solver_opts *o, const double *U_n,
+                      const double *U_nm1, const double *forcing, const double *bc, double *U_np1,
+                      chns_step_stats *stats, void *stream) {
+  TRY(check_params(mc, p));
+  return step_impl(const_cast<chns_mesh *>(mc), p, o, U_n, U_nm1, forcing, bc, U_np1, stats, S(stream));
+}
+
+chns_status chns_energy_mass(const chns_mesh *mc, const chns_params *p, const double *U, double *energy,
+                             double *mass, double *bubble_mass, void *stream) {
+  TRY(check_params(mc, p));
+  if (!U) { set_error("null vector"); return CHNS_ERR_ARG; }
+  double em[3];
+  TRY(energy_mass_impl(const_cast<chns_mesh *>(mc), p, U, em, S(stream)));
+  if (energy) *energy = em[0];
+  if (mass) *mass = em[1];
+  if (bubble_mass) *bubble_mass = em[2];
+  return CHNS_OK;
+}
+
+chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params *params, chns_batch **out) {
+  if (!out || n <= 0 || !meshes || !params) { set_error("invalid batch arguments"); return CHNS_ERR_ARG; }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) TRY(check_params(meshes[i], &params[i]));
+  chns_batch *b = new chns_batch;
+  b->meshes.assign(meshes, meshes + n);
+  b->params.assign(params, params + n);
+  *out = b;
+  return CHNS_OK;
+}
+
+chns_status chns_batch_step(chns_batch *b, const chns_solver_opts *o, double *const *U_n, double *const *U_nm1,
+                            double *const *U_np1, chns_step_stats *stats, void *stream) {
+  if (!b || !o || !U_n || !U_np1) { set_error("null argument"); return CHNS_ERR_ARG; }
+  for (size_t i = 0; i < b->meshes.size(); ++i) {
+    chns_status s = step_impl(b->meshes[i], &b->params[i], o, U_n[i], U_nm1 ? U_nm1[i] : nullptr, nullptr,
+                              nullptr, U_np1[i], stats ? &stats[i] : nullptr, S(stream));
+    if (s != CHNS_OK) {
+      std::string msg = std::string("instance ") + std::to_string(i) + ": " + chns::last_error();
+      set_error("%s", msg.c_str());
+      return s;
+    }
+  }
+  return CHNS_OK;
+}
+
+void chns_batch_destroy(chns_batch *b) { delete b; }
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of libchns.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/chns.h"
+
+namespace chns {
+
+void set_error(const char *fmt, ...);
+void note_launches(int n);  // tracing counter of kernel launches
+
+#define CHNS_CUDA_TRY(expr)                                                      \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ::chns::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                     \
+      return e_ == cudaErrorMemoryAllocation ? CHNS_ERR_OOM : CHNS_ERR_CUDA;     \
+    }                                                                            \
+  } while (0)
+
+// Device buffer owned by the library.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  chns_status ensure(size_t n);
+  void release();
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Element-kernel coefficients that do not depend on the element.
+struct PhysCoef {
+  double dt, inv_dt, four_dt2;
+  double alpha, beta, gamma, xi;   // rho = alpha phi* + beta, eta = gamma phi* + xi
+  double jc;                       // flux J = jc grad mu, jc = (rho_r - 1)/2
+  double inv_Pe, inv_We, inv_Re, inv_Fr, CnWe, inv_PeCn, Cn2, C_I;
+  double g[3];
+  double ext[3];                   // box extent per axis
+  double lo[3];
+};
+
+PhysCoef make_coef(const chns_params &p, const double *lo, const double *hi);
+
+// Solver scratch, sized on first use.
+struct Workspace {
+  DevBuf ut, dl, ut32, dl32, f;        // prepared nodal fields (time averages / increments)
+  DevBuf F, dU, r;                     // double n_dof
+  DevBuf V;                            // double (m+1) n_dof Krylov basis
+  DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
+  DevBuf wv, yv;                       // float/double n_dof work vectors
+  DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks
+  DevBuf red;                          // reduction partials
+  DevBuf hdev;                         // device copy of Gram-Schmidt coefficients
+  double *hpinned = nullptr;           // pinned host mirror of reduction results
+  std::vector<cudaEvent_t> ev;
+  ~Workspace();
+};
+
+}  // namespace chns
+
+struct chns_mesh {
+  int dim = 0, max_level = 0, nc = 0, nf = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  int64_t n_elem = 0, n_nodes = 0, n_hang = 0;
+  bool uniform = false;
+  int n_colours = 0;
+  std::vector<int64_t> colour_start;   // n_colours + 1, elements are stored colour by colour
+  int n_node_colours = 0;
+  std::vector<int64_t> node_colour_start;  // nodes of each node colour (for probing)
+  int64_t origin = -1;                 // node at the box origin (pressure pin)
+  int64_t n_wall = 0;
+  std::vector<int64_t> node_xyz;       // host: n_nodes * dim integer coordinates
+  // device arrays
+  int32_t *conn = nullptr;             // n_elem * nc: node index, or -(h+1) for hanging corner h
+  uint8_t *level = nullptr;            // n_elem
+  uint32_t *anchor = nullptr;          // n_elem * dim
+  int32_t *hang = nullptr;             // n_hang * 4 parent nodes (-1 padded for edge midpoints)
+  int32_t *wall = nullptr;             // n_wall node indices on the box boundary
+  int32_t *node_perm = nullptr;        // n_nodes node indices grouped by node colour
+  int device = 0;
+  chns::Workspace ws;
+};
+
+struct chns_batch {
+  std::vector<chns_mesh *> meshes;
+  std::vector<chns_params> params;
+};

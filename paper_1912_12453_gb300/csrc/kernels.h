@@ -1,0 +1,27 @@
+// Host-side launchers of the device kernels (element.cu, vector.cu).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "chns_internal.h"
+
+namespace chns {
+
+template <typename T>
+void launch_prep(const chns_mesh *m, const double *Un, const double *Uo, T *ut, T *dl, cudaStream_t st);
+template <typename T>
+void launch_cast(const double *x, int64_t n, T *y, cudaStream_t st);
+void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
+                     const double *f, double *F, cudaStream_t st);
+template <typename T>
+void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *y,
+                   cudaStream_t st);
+void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st);
+template <typename T>
+void launch_dirichlet_jv(const chns_mesh *m, const T *w, T *y, cudaStream_t st);
+int64_t energy_blocks(const chns_mesh *m);
+void launch_energy(const chns_mesh *m, const PhysCoef &pc, const double *U, double *partial, cudaStream_t st);
+
+}  // namespace chns

@@ -1,0 +1,468 @@
+// Mesh construction from octree leaves (Sec. 4 "Meshing", "Handling hanging
+// nodes", "2:1 Balancing"): validation, node numbering, hanging-node
+// constraints, element and node colourings, upload to the device.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "chns_internal.h"
+
+namespace chns {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+chns_status DevBuf::ensure(size_t n) {
+  if (n <= bytes && p) return CHNS_OK;
+  release();
+  if (n == 0) return CHNS_OK;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    set_error("cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CHNS_ERR_OOM : CHNS_ERR_CUDA;
+  }
+  bytes = n;
+  return CHNS_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+Workspace::~Workspace() {
+  for (auto e : ev) cudaEventDestroy(e);
+  if (hpinned) cudaFreeHost(hpinned);
+}
+
+namespace {
+
+// Open-addressing hash map from a 64-bit key to a 32-bit value.
+class KeyMap {
+ public:
+  explicit KeyMap(size_t expected) {
+    size_t cap = 16;
+    while (cap < expected * 2) cap <<= 1;
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, 0);
+    mask_ = cap - 1;
+  }
+  // returns (value, inserted)
+  std::pair<int64_t, bool> insert(uint64_t key, int64_t value) {
+    size_t i = hash(key) & mask_;
+    while (true) {
+      if (keys_[i] == kEmpty) {
+        keys_[i] = key;
+        vals_[i] = value;
+        ++size_;
+        return {value, true};
+      }
+      if (keys_[i] == key) return {vals_[i], false};
+      i = (i + 1) & mask_;
+    }
+  }
+  int64_t find(uint64_t key) const {
+    size_t i = hash(key) & mask_;
+    while (true) {
+      if (keys_[i] == kEmpty) return -1;
+      if (keys_[i] == key) return vals_[i];
+      i = (i + 1) & mask_;
+    }
+  }
+  size_t size() const { return size_; }
+
+ private:
+  static constexpr uint64_t kEmpty = ~uint64_t(0);
+  static uint64_t hash(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int64_t> vals_;
+  size_t mask_ = 0, size_ = 0;
+};
+
+inline uint64_t pack(const int64_t *x, int dim) {
+  uint64_t k = 0;
+  for (int a = 0; a < dim; ++a) k |= uint64_t(x[a]) << (21 * a);
+  return k;
+}
+
+// octant key: the doubled coordinates of its centre, 2 x + s (unique per
+// octant, < 2^21 per axis for max_level <= 20)
+inline uint64_t okey(int level, const int64_t *x, int dim, int max_level) {
+  int64_t c[3];
+  int64_t s = int64_t(1) << (max_level - level);
+  for (int a = 0; a < dim; ++a) c[a] = 2 * x[a] + s;
+  return pack(c, dim);
+}
+
+uint64_t morton(const uint32_t *a, int dim, int max_level) {
+  uint64_t k = 0;
+  for (int b = 0; b <= max_level; ++b)
+    for (int ax = 0; ax < dim; ++ax) k |= uint64_t((a[ax] >> b) & 1u) << (dim * b + ax);
+  return k;
+}
+
+template <class T>
+chns_status upload(T **dst, const std::vector<T> &src) {
+  if (src.empty()) { *dst = nullptr; return CHNS_OK; }
+  CHNS_CUDA_TRY(cudaMalloc((void **)dst, sizeof(T) * src.size()));
+  CHNS_CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return CHNS_OK;
+}
+
+}  // namespace
+
+chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor,
+                       int max_level, const double lo[3], const double hi[3], chns_mesh *m) {
+  if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return CHNS_ERR_ARG; }
+  if (n <= 0 || !level || !anchor) { set_error("no leaves"); return CHNS_ERR_ARG; }
+  if (max_level < 0 || max_level > 20) { set_error("max_level must be in [0, 20]"); return CHNS_ERR_ARG; }
+  if (n > (int64_t(1) << 31) / 8) { set_error("too many leaves"); return CHNS_ERR_ARG; }
+  m->dim = dim;
+  m->max_level = max_level;
+  m->nc = 1 << dim;
+  m->nf = dim + 3;
+  m->n_elem = n;
+  for (int a = 0; a < 3; ++a) {
+    m->lo[a] = lo ? lo[a] : 0.0;
+    m->hi[a] = hi ? hi[a] : 1.0;
+    if (a < dim && !(m->hi[a] > m->lo[a])) { set_error("empty box"); return CHNS_ERR_ARG; }
+  }
+  const int nc = m->nc;
+  const int64_t top = int64_t(1) << max_level;
+
+  // --- leaves: alignment, Morton order, exact tiling of the box
+  uint64_t expect = 0;
+  bool uniform = true;
+  for (int64_t e = 0; e < n; ++e) {
+    int l = level[e];
+    if (l > max_level) { set_error("leaf %lld: level %d > max_level", (long long)e, l); return CHNS_ERR_MESH; }
+    if (l != level[0]) uniform = false;
+    int64_t s = int64_t(1) << (max_level - l);
+    for (int a = 0; a < dim; ++a) {
+      int64_t x = anchor[e * dim + a];
+      if (x % s != 0 || x + s > top) {
+        set_error("leaf %lld: anchor not aligned to its level or outside the box", (long long)e);
+        return CHNS_ERR_MESH;
+      }
+    }
+    uint64_t k = morton(anchor + e * dim, dim, max_level);
+    if (k != expect) {
+      set_error("leaves are not in Morton order or do not tile the box (leaf %lld)", (long long)e);
+      return CHNS_ERR_MESH;
+    }
+    expect = k + (uint64_t(1) << (dim * (max_level - l)));
+  }
+  if (expect != (uint64_t(1) << (dim * max_level))) {
+    set_error("leaves do not cover the box");
+    return CHNS_ERR_MESH;
+  }
+  m->uniform = uniform;
+
+  // --- 2:1 balance across faces, edges and corners: every same-level
+  // neighbour of a leaf has its parent among the leaves or their ancestors.
+  {
+    KeyMap oct(size_t(n) * 2);
+    for (int64_t e = 0; e < n; ++e) {
+      int64_t x[3];
+      for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a];
+      int l = level[e];
+      oct.insert(okey(l, x, dim, max_level), 1);
+      while (l > 0) {
+        --l;
+        int64_t s = int64_t(1) << (max_level - l);
+        for (int a = 0; a < dim; ++a) x[a] = (x[a] / s) * s;
+        if (!oct.insert(okey(l, x, dim, max_level), 1).second) break;
+      }
+    }
+    int nnb = dim == 2 ? 9 : 27;
+    for (int64_t e = 0; e < n; ++e) {
+      int l = level[e];
+      if (l <= 1) continue;
+      int64_t s = int64_t(1) << (max_level - l);
+      int64_t ps = s * 2;
+      for (int q = 0; q < nnb; ++q) {
+        int64_t x[3];
+        int t = q;
+        bool self = true, inside = true;
+        for (int a = 0; a < dim; ++a) {
+          int o = t % 3 - 1;
+          t /= 3;
+          if (o) self = false;
+          x[a] = int64_t(anchor[e * dim + a]) + o * s;
+          if (x[a] < 0 || x[a] >= top) inside = false;
+        }
+        if (self || !inside) continue;
+        for (int a = 0; a < dim; ++a) x[a] = (x[a] / ps) * ps;
+        if (oct.find(okey(l - 1, x, dim, max_level)) < 0) {
+          set_error("mesh is not 2:1 balanced at leaf %lld", (long long)e);
+          return CHNS_ERR_MESH;
+        }
+      }
+    }
+  }
+
+  // --- nodes: unique corners in first-appearance order
+  KeyMap nodes(size_t(n) * (dim == 2 ? 2 : 3) + 64);
+  std::vector<int64_t> all_xyz;
+  std::vector<int32_t> corner_all(size_t(n) * nc);
+  all_xyz.reserve(size_t(n) * (dim == 2 ? 2 : 3) * dim);
+  for (int64_t e = 0; e < n; ++e) {
+    int64_t s = int64_t(1) << (max_level - level[e]);
+    for (int c = 0; c < nc; ++c) {
+      int64_t x[3];
+      for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a] + (((c >> a) & 1) ? s : 0);
+      auto r = nodes.insert(pack(x, dim), (int64_t)(all_xyz.size() / dim));
+      if (r.second)
+        for (int a = 0; a < dim; ++a) all_xyz.push_back(x[a]);
+      corner_all[e * nc + c] = (int32_t)r.first;
+    }
+  }
+  const int64_t n_all = (int64_t)(all_xyz.size() / dim);
+
+  // --- hanging nodes: a node at the midpoint of an edge, or the centre of a
+  // face, of some leaf; constrained to the mean of that edge's / face's corners
+  std::vector<int32_t> hang_of(n_all, -1);
+  std::vector<int32_t> hang_par;  // 4 per hanging node, all-node ids
+  for (int64_t e = 0; e < n; ++e) {
+    if (level[e] >= max_level) continue;
+    int64_t s = int64_t(1) << (max_level - level[e]);
+    int npat = dim == 2 ? 9 : 27;
+    for (int pat = 0; pat < npat; ++pat) {
+      int ch[3], t = pat, nhalf = 0;
+      for (int a = 0; a < dim; ++a) { ch[a] = t % 3; t /= 3; nhalf += ch[a] == 1; }
+      if (nhalf == 0 || nhalf == dim) continue;
+      int64_t x[3];
+      for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a] + ch[a] * (s / 2);
+      int64_t id = nodes.find(pack(x, dim));
+      if (id < 0) continue;
+      int32_t par[4] = {-1, -1, -1, -1};
+      for (int b = 0; b < (1 << nhalf); ++b) {
+        int64_t y[3];
+        int bit = 0;
+        for (int a = 0; a < dim; ++a) {
+          if (ch[a] == 1) y[a] = anchor[e * dim + a] + (((b >> bit++) & 1) ? s : 0);
+          else y[a] = anchor[e * dim + a] + (ch[a] == 2 ? s : 0);
+        }
+        int64_t pid = nodes.find(pack(y, dim));
+        if (pid < 0) { set_error("hanging node parent missing (mesh not conforming)"); return CHNS_ERR_MESH; }
+        par[b] = (int32_t)pid;
+      }
+      std::sort(par, par + (1 << nhalf));
+      if (hang_of[id] < 0) {
+        hang_of[id] = (int32_t)(hang_par.size() / 4);
+        hang_par.insert(hang_par.end(), par, par + 4);
+      } else {
+        const int32_t *q = &hang_par[size_t(hang_of[id]) * 4];
+        for (int b = 0; b < 4; ++b)
+          if (q[b] != par[b]) { set_error("inconsistent hanging-node constraint"); return CHNS_ERR_MESH; }
+      }
+    }
+  }
+  const int64_t n_hang = (int64_t)(hang_par.size() / 4);
+  for (int64_t h = 0; h < n_hang * 4; ++h)
+    if (hang_par[h] >= 0 && hang_of[hang_par[h]] >= 0) {
+      set_error("hanging node constrained by another hanging node (mesh not 2:1 balanced)");
+      return CHNS_ERR_MESH;
+    }
+
+  // --- independent node numbering (first-appearance order)
+  std::vector<int32_t> indep_id(n_all, -1);
+  int64_t n_nodes = 0;
+  std::vector<int64_t> node_xyz;
+  node_xyz.reserve(size_t(n_all - n_hang) * dim);
+  for (int64_t i = 0; i < n_all; ++i)
+    if (hang_of[i] < 0) {
+      indep_id[i] = (int32_t)n_nodes++;
+      for (int a = 0; a < dim; ++a) node_xyz.push_back(all_xyz[i * dim + a]);
+    }
+  std::vector<int32_t> hang_dev(size_t(n_hang) * 4);
+  for (int64_t h = 0; h < n_hang * 4; ++h) hang_dev[h] = hang_par[h] >= 0 ? indep_id[hang_par[h]] : -1;
+  std::vector<int32_t> conn(size_t(n) * nc);
+  for (int64_t k = 0; k < n * nc; ++k) {
+    int32_t id = corner_all[k];
+    conn[k] = hang_of[id] >= 0 ? -(hang_of[id] + 1) : indep_id[id];
+  }
+  std::vector<int32_t> wall;
+  m->origin = -1;
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    bool w = false, org = true;
+    for (int a = 0; a < dim; ++a) {
+      int64_t c = node_xyz[i * dim + a];
+      if (c == 0 || c == top) w = true;
+      if (c != 0) org = false;
+    }
+    if (w) wall.push_back((int32_t)i);
+    if (org) m->origin = i;
+  }
+
+  // --- expanded footprints (independent nodes an element reads / writes)
+  auto footprint = [&](int64_t e, int32_t *out) {
+    int k = 0;
+    for (int c = 0; c < nc; ++c) {
+      int32_t v = conn[e * nc + c];
+      if (v >= 0) out[k++] = v;
+      else
+        for (int b = 0; b < 4; ++b) {
+          int32_t p = hang_dev[size_t(-v - 1) * 4 + b];
+          if (p >= 0) out[k++] = p;
+        }
+    }
+    std::sort(out, out + k);
+    return int(std::unique(out, out + k) - out);
+  };
+
+  // --- element colouring: same colour => disjoint footprints
+  std::vector<int> ecol(n);
+  int n_col = 0;
+  if (uniform) {
+    int64_t s = int64_t(1) << (max_level - level[0]);
+    for (int64_t e = 0; e < n; ++e) {
+      int c = 0;
+      for (int a = 0; a < dim; ++a) c |= int((anchor[e * dim + a] / s) & 1) << a;
+      ecol[e] = c;
+    }
+    n_col = nc;
+  } else {
+    // node -> elements incidence over footprints
+    std::vector<int64_t> start(n_nodes + 1, 0);
+    std::vector<int32_t> fp(32);
+    for (int64_t e = 0; e < n; ++e) {
+      int k = footprint(e, fp.data());
+      for (int i = 0; i < k; ++i) start[fp[i] + 1]++;
+    }
+    for (int64_t i = 0; i < n_nodes; ++i) start[i + 1] += start[i];
+    std::vector<int32_t> elems(start[n_nodes]);
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t e = 0; e < n; ++e) {
+      int k = footprint(e, fp.data());
+      for (int i = 0; i < k; ++i) elems[fill[fp[i]]++] = (int32_t)e;
+    }
+    std::vector<int64_t> mark(256, -1);
+    std::fill(ecol.begin(), ecol.end(), -1);
+    for (int64_t e = 0; e < n; ++e) {
+      int k = footprint(e, fp.data());
+      for (int i = 0; i < k; ++i)
+        for (int64_t t = start[fp[i]]; t < start[fp[i] + 1]; ++t) {
+          int c = ecol[elems[t]];
+          if (c >= 0) mark[c] = e;
+        }
+      int c = 0;
+      while (c < 256 && mark[c] == e) ++c;
+      if (c == 256) { set_error("element colouring needs more than 256 colours"); return CHNS_ERR_MESH; }
+      ecol[e] = c;
+      n_col = std::max(n_col, c + 1);
+    }
+  }
+  // elements sorted by colour, Morton order within a colour
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return ecol[a] < ecol[b]; });
+  m->n_colours = n_col;
+  m->colour_start.assign(n_col + 1, 0);
+  for (int64_t e = 0; e < n; ++e) m->colour_start[ecol[e] + 1]++;
+  for (int c = 0; c < n_col; ++c) m->colour_start[c + 1] += m->colour_start[c];
+  std::vector<int32_t> conn_s(size_t(n) * nc);
+  std::vector<uint8_t> lev_s(n);
+  std::vector<uint32_t> anc_s(size_t(n) * dim);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t e = order[i];
+    for (int c = 0; c < nc; ++c) conn_s[i * nc + c] = conn[e * nc + c];
+    lev_s[i] = level[e];
+    for (int a = 0; a < dim; ++a) anc_s[i * dim + a] = anchor[e * dim + a];
+  }
+
+  // --- node colouring: nodes of one colour never share an element footprint
+  // (probing of the nodal diagonal blocks)
+  std::vector<int> ncol(n_nodes, -1);
+  int n_ncol = 0;
+  if (uniform) {
+    int64_t s = int64_t(1) << (max_level - level[0]);
+    for (int64_t i = 0; i < n_nodes; ++i) {
+      int c = 0;
+      for (int a = 0; a < dim; ++a) c |= int((node_xyz[i * dim + a] / s) & 1) << a;
+      ncol[i] = c;
+    }
+    n_ncol = nc;
+  } else {
+    std::vector<int64_t> start(n_nodes + 1, 0);
+    std::vector<int32_t> fp(32);
+    for (int64_t e = 0; e < n; ++e) {
+      int k = footprint(e, fp.data());
+      for (int i = 0; i < k; ++i) start[fp[i] + 1]++;
+    }
+    for (int64_t i = 0; i < n_nodes; ++i) start[i + 1] += start[i];
+    std::vector<int32_t> elems(start[n_nodes]);
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t e = 0; e < n; ++e) {
+      int k = footprint(e, fp.data());
+      for (int i = 0; i < k; ++i) elems[fill[fp[i]]++] = (int32_t)e;
+    }
+    std::vector<int64_t> mark(256, -1);
+    for (int64_t a = 0; a < n_nodes; ++a) {
+      for (int64_t t = start[a]; t < start[a + 1]; ++t) {
+        int k = footprint(elems[t], fp.data());
+        for (int i = 0; i < k; ++i) {
+          int c = ncol[fp[i]];
+          if (c >= 0) mark[c] = a;
+        }
+      }
+      int c = 0;
+      while (c < 256 && mark[c] == a) ++c;
+      if (c == 256) { set_error("node colouring needs more than 256 colours"); return CHNS_ERR_MESH; }
+      ncol[a] = c;
+      n_ncol = std::max(n_ncol, c + 1);
+    }
+  }
+  std::vector<int32_t> nperm(n_nodes);
+  std::iota(nperm.begin(), nperm.end(), 0);
+  std::stable_sort(nperm.begin(), nperm.end(), [&](int32_t a, int32_t b) { return ncol[a] < ncol[b]; });
+  m->n_node_colours = n_ncol;
+  m->node_colour_start.assign(n_ncol + 1, 0);
+  for (int64_t i = 0; i < n_nodes; ++i) m->node_colour_start[ncol[i] + 1]++;
+  for (int c = 0; c < n_ncol; ++c) m->node_colour_start[c + 1] += m->node_colour_start[c];
+
+  m->n_nodes = n_nodes;
+  m->n_hang = n_hang;
+  m->n_wall = (int64_t)wall.size();
+  m->node_xyz = std::move(node_xyz);
+
+  chns_status st;
+  CHNS_CUDA_TRY(cudaGetDevice(&m->device));
+  if ((st = upload(&m->conn, conn_s)) != CHNS_OK) return st;
+  if ((st = upload(&m->level, lev_s)) != CHNS_OK) return st;
+  if ((st = upload(&m->anchor, anc_s)) != CHNS_OK) return st;
+  if ((st = upload(&m->hang, hang_dev)) != CHNS_OK) return st;
+  if ((st = upload(&m->wall, wall)) != CHNS_OK) return st;
+  if ((st = upload(&m->node_perm, nperm)) != CHNS_OK) return st;
+  return CHNS_OK;
+}
+
+}  // namespace chns

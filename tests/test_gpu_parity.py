@@ -1,0 +1,175 @@
+"""CUDA path against the oracle, element by element, on seeded inputs.
+
+Tolerances (norm-wise relative 2-norm): FP64 apply 1e-12, FP32-bulk apply
+1e-5, converged step 1e-9.
+"""
+import numpy as np
+import pytest
+
+from paper_1912_12453_gb300 import workloads as W
+from tests.harness import Pair, rel, random_state, physical_state
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32, TOLSTEP = 1e-12, 1e-5, 1e-9
+
+
+def _params(dim, **kw):
+    base = dict(dt=1e-2, Cn=0.3, Re=7.0, We=3.0, Pe=5.0, Fr=2.0, rho_ratio=0.3, eta_ratio=0.6)
+    base.update(kw)
+    g = (0.6, -0.8, 0.0) if dim == 2 else (0.48, -0.6, 0.64)
+    return W.Params(dim, gravity=g, **base)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1912_12453_gb300 import build
+    build.build()
+
+
+def _meshes():
+    return {
+        "u2_l1": W.uniform_leaves(2, 1),
+        "u2_l3": W.uniform_leaves(2, 3),
+        "hang2": W.tiny_leaves(2, "hang"),
+        "front2": W.half_refined_leaves(2, 3),
+        "band2": W.band_leaves(2, 3, 6, [W.Sphere((0.45, 0.55), 0.2)], 0.03),
+        "u3_l1": W.uniform_leaves(3, 1),
+        "u3_l2": W.uniform_leaves(3, 2),
+        "hang3": W.tiny_leaves(3, "hang"),
+        "front3": W.half_refined_leaves(3, 2),
+        "band3": W.band_leaves(3, 2, 5, [W.Sphere((0.5, 0.45, 0.4), 0.25)], 0.04),
+    }
+
+
+MESHES = list(_meshes().keys())
+
+
+@pytest.fixture(scope="module")
+def pairs():
+    return {k: Pair(v) for k, v in _meshes().items()}
+
+
+@pytest.mark.parametrize("name", MESHES)
+def test_mesh_nodes_match_oracle(pairs, name):
+    p = pairs[name]
+    assert p.gm.n_nodes == p.om.n_nodes
+    assert p.gm.n_hanging == p.om.n_hanging
+    assert p.gm.n_dof == p.om.n_dof
+
+
+@pytest.mark.parametrize("name", MESHES)
+@pytest.mark.parametrize("with_data", [False, True])
+def test_residual_fp64(pairs, name, with_data):
+    p = pairs[name]
+    dim = p.om.dim
+    prm = _params(dim)
+    Un = random_state(p.om.n_nodes, p.nf, 1)
+    Uo = random_state(p.om.n_nodes, p.nf, 2)
+    f = random_state(p.om.n_nodes, p.nf, 3) if with_data else None
+    g = random_state(p.om.n_nodes, p.nf, 4) if with_data else None
+    ref = p.om.residual(prm, Un, Uo, f, g)
+    got = p.chns.residual(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo),
+                          None if f is None else p.to_gpu(f), None if g is None else p.to_gpu(g))
+    assert rel(p.to_oracle(got), ref) <= TOL64
+
+
+@pytest.mark.parametrize("name", MESHES)
+def test_jacvec_fp64(pairs, name):
+    p = pairs[name]
+    prm = _params(p.om.dim)
+    Un = random_state(p.om.n_nodes, p.nf, 5)
+    Uo = random_state(p.om.n_nodes, p.nf, 6)
+    w = random_state(p.om.n_nodes, p.nf, 7, -1, 1)
+    ref = p.om.jacvec(prm, Un, Uo, w)
+    got = p.chns.jacvec(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w))
+    assert rel(p.to_oracle(got), ref) <= TOL64
+
+
+@pytest.mark.parametrize("name", MESHES)
+def test_jacvec_fp32_bulk(pairs, name):
+    import torch
+    p = pairs[name]
+    wl = W.workload("droplet2d_l5" if p.om.dim == 2 else "droplet3d_l6")
+    prm = wl.params
+    Uo, Un = physical_state(p.om, wl)
+    w = W.perturbation(p.om.n_nodes, p.nf, 2)[1]
+    ref = p.om.jacvec(prm, Un, Uo, w)
+    got = p.chns.jacvec(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32), precision="fp32")
+    assert rel(p.to_oracle(got), ref) <= TOL32
+
+
+@pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "band3"])
+def test_energy_mass(pairs, name):
+    p = pairs[name]
+    prm = _params(p.om.dim)
+    U = random_state(p.om.n_nodes, p.nf, 8)
+    ref = p.om.energy_mass(prm, U)
+    got = p.chns.energy_mass(p.gm, prm, p.to_gpu(U))
+    for a, b in zip(got, ref):
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(b))
+
+
+@pytest.mark.parametrize("name", ["band2", "front3"])
+def test_init_mu(pairs, name):
+    p = pairs[name]
+    prm = _params(p.om.dim)
+    U = random_state(p.om.n_nodes, p.nf, 9, -1, 1)
+    ref = p.om.init_mu(prm, U)
+    t = p.to_gpu(U)
+    p.chns.init_mu(p.gm, prm, t)
+    assert rel(p.to_oracle(t), ref) <= 1e-10
+
+
+def _inv_norm(J, seed=0, its=25):
+    """||J^{-1}||_2 by power iteration on J^{-T} J^{-1} (sparse LU)."""
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(J.tocsc())
+    x = np.random.default_rng(seed).standard_normal(J.shape[0])
+    for _ in range(its):
+        x = lu.solve(lu.solve(x), trans="T")
+        x /= np.linalg.norm(x)
+    return float(np.linalg.norm(lu.solve(x)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["band2", "band3"])
+def test_step_matches_oracle(pairs, name, precision):
+    """One CN step from the droplet's initial state.
+
+    The GPU state must be a root of the oracle's residual (to 1e-13 of the
+    initial residual), v, phi and mu must match the oracle's Newton root to
+    1e-9, and the whole state (pressure included) must lie within the
+    first-order bound ||J^-1|| (||F(U_gpu)|| + ||F(U_ref)||): the PSPG block
+    scales the pressure by tau_m/(rho We), so ||J^-1|| reaches ~1e8 along a
+    pressure direction and rounding-level residuals move p that far.
+    """
+    import torch
+    p = pairs[name]
+    wl = W.workload("droplet2d_l5" if p.om.dim == 2 else "droplet3d_l6")
+    prm = wl.params
+    U0 = W.initial_state(p.om.coords, wl)
+    U0 = p.om.init_mu(prm, U0)
+    ref, st = p.om.step(prm, U0, rtol=1e-14, atol=1e-16)
+    t0 = p.to_gpu(U0)
+    out = torch.empty_like(t0)
+    opts = p.chns.SolverOpts.make(precision=precision, newton_rtol=1e-14, newton_atol=1e-16,
+                                  krylov_rtol=1e-10 if precision == "fp64" else 1e-6, newton_max_it=30)
+    stats = p.chns.step(p.gm, prm, t0, out, opts)
+    assert stats["newton_its"] >= 1
+    got = p.to_oracle(out)
+    F0 = np.linalg.norm(p.om.residual(prm, U0, U0))
+    Fg = np.linalg.norm(p.om.residual(prm, got, U0))
+    Fr = np.linalg.norm(p.om.residual(prm, ref, U0))
+    assert Fg <= 1e-13 * F0
+    d = (got - ref).reshape(-1, p.nf)
+    r = ref.reshape(-1, p.nf)
+    dim = p.om.dim
+    for k in list(range(dim)) + [dim + 1, dim + 2]:
+        assert np.linalg.norm(d[:, k]) <= TOLSTEP * max(np.linalg.norm(r[:, k]), 1e-30) + 1e-14, k
+    bound = 2.0 * _inv_norm(p.om.jacobian(prm, ref, U0)) * (Fg + Fr)
+    assert np.linalg.norm(d) <= bound + TOLSTEP * np.linalg.norm(r)
+    assert abs(stats["mass_new"] - stats["mass_old"]) < 1e-12
