@@ -45,6 +45,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 HBM_PEAK_FALLBACK = 6800.0
 
 
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -176,6 +180,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 CN steps (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-applies", type=int, default=2)
+    ap.add_argument("--newton-rtol", type=float, default=1e-7)
+    ap.add_argument("--krylov-max-it", type=int, default=400)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -238,19 +244,23 @@ def main():
                 times.append(e0.elapsed_time(e1))
         return float(np.mean(times)), float(np.median(times))
 
+    log(f"mesh: {mesh.n_elem} elements, {n_dof} DoF, {mesh.n_colours} colours")
     jv32_mean, jv32_med = sweep("fp32")
+    log(f"apply sweep fp32 J.w {jv32_mean:.3f} ms")
     jv64_mean, jv64_med = sweep("fp64", "jacvec") if nvec > 0 else (None, None)
     res64_mean, _ = sweep("fp64", "residual") if nvec > 0 else (None, None)
+    log(f"apply sweep fp64 J.w {jv64_mean} ms, residual {res64_mean} ms")
 
     # ---- CN steps, FP32-bulk mixed (timed region)
-    opts32 = chns.SolverOpts.make(precision="fp32", newton_rtol=wl.newton_rtol, krylov_rtol=1e-3,
-                                  krylov_restart=30, krylov_max_it=1000)
-    opts64 = chns.SolverOpts.make(precision="fp64", newton_rtol=wl.newton_rtol, krylov_rtol=1e-3,
-                                  krylov_restart=30, krylov_max_it=1000)
+    opts32 = chns.SolverOpts.make(precision="fp32", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
+                                  krylov_restart=30, krylov_max_it=args.krylov_max_it)
+    opts64 = chns.SolverOpts.make(precision="fp64", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
+                                  krylov_restart=30, krylov_max_it=args.krylov_max_it)
     Ua = U0.clone()
     Ub = torch.empty_like(Ua)
     for _ in range(args.warmup):
-        chns.step(mesh, prm, Ua, Ub, opts32)
+        st = chns.step(mesh, prm, Ua, Ub, opts32)
+        log("warm-up fp32 step", {k: st[k] for k in ("newton_its", "krylov_its_total", "seconds")})
         Ua, Ub = Ub, Ua
     Ua.copy_(U0)
     barrier()
@@ -265,6 +275,7 @@ def main():
         e1.record(stream)
         barrier()
     step32_ms = e0.elapsed_time(e1) / args.steps
+    log("fp32 steps", [{k: st[k] for k in ("newton_its", "krylov_its_total", "seconds")} for st in stats32])
     launches = chns.kernel_launches() - launches0
     U32 = Ua.clone()
     jv_ms = sum(s["jacvec_ms"] for s in stats32)
@@ -294,6 +305,7 @@ def main():
         e0.record(stream)
         for _ in range(k64):
             stats64.append(chns.step(mesh, prm, Ua, Ub, opts64))
+            log("fp64 step", {k: stats64[-1][k] for k in ("newton_its", "krylov_its_total", "seconds")})
             Ua, Ub = Ub, Ua
         e1.record(stream)
         barrier()
@@ -347,6 +359,7 @@ def main():
             "config": {"workload": "3D droplet, uniform octree level 6 (64^3 hexes, 274,625 nodes, "
                                    "1,647,750 DoF), Cn 0.02, Re 100, We 50, ratios 1e-2, dt 5e-4",
                        "precision": "FP32 element J.w + FP32 block-Jacobi inside FP64 Newton / FP64 Gram-Schmidt",
+                       "newton_rtol": args.newton_rtol,
                        "l2": "step working set (Krylov basis 31 x 13 MB) > L2; apply sweep flushes L2",
                        "parallelism": f"replicas x{world}"},
             "cn_step": {

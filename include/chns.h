@@ -92,7 +92,8 @@ typedef struct {
   int jacvec_calls;
   double residual_ms;              /* device time of the FP64 residual applies */
   int residual_calls;
-  double precond_ms;               /* device time of building the block-Jacobi preconditioner */
+  double precond_ms;               /* host time of building the block-Jacobi preconditioner */
+  int fp64_newton_its;             /* CHNS_FP32_BULK: Newton iterations finished with FP64 J.w */
 } chns_step_stats;
 
 /* ---------------------------------------------------------------- meshes */
@@ -154,8 +155,12 @@ chns_status chns_init_mu(const chns_mesh *mesh, const chns_params *params, doubl
  * right-preconditioned FGMRES(m) with nodal block-Jacobi.  The residual and
  * the Newton update are double; with CHNS_FP32_BULK the Krylov J.w and
  * preconditioner run in float and the Gram-Schmidt inner products and norms
- * stay double (iterative refinement by the outer double residual).  U_np1
- * receives the result (may not alias U_n).  stats (host, nullable). */
+ * stay double (iterative refinement by the outer double residual); once a
+ * float-Krylov Newton iteration cuts ||F|| by less than 10x, the remaining
+ * iterations apply J in double with the float preconditioner promoted.  U_np1
+ * receives the result (may not alias U_n).  stats (host, nullable).  Setting
+ * the environment variable CHNS_TRACE=1 prints each Newton iteration to
+ * stderr. */
 chns_status chns_step(const chns_mesh *mesh, const chns_params *params,
                       const chns_solver_opts *opts, const double *U_n, const double *U_nm1,
                       const double *forcing, const double *bc, double *U_np1,

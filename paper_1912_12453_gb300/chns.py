@@ -67,7 +67,8 @@ class StepStats(ctypes.Structure):
                 ("mass_old", ctypes.c_double), ("mass_new", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("jacvec_ms", ctypes.c_double),
                 ("jacvec_calls", ctypes.c_int), ("residual_ms", ctypes.c_double),
-                ("residual_calls", ctypes.c_int), ("precond_ms", ctypes.c_double)]
+                ("residual_calls", ctypes.c_int), ("precond_ms", ctypes.c_double),
+                ("fp64_newton_its", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -2,6 +2,8 @@
 // (Sec. 3.5), diagnostics and batches.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -150,14 +152,15 @@ struct Timer {
 // indicator of one field on the nodes of one node colour: nodes of a colour
 // never share an element, so each probed node sees only its own block.
 template <typename T>
-chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, cudaStream_t st) {
+chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, DevBuf &out,
+                               cudaStream_t st) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
-  TRY(ws.binv.ensure(sizeof(T) * m->n_nodes * nf * nf + 16));
+  TRY(out.ensure(sizeof(T) * m->n_nodes * nf * nf + 16));
   TRY(ws.wv.ensure(sizeof(T) * n));
   TRY(ws.yv.ensure(sizeof(T) * n));
-  T *w = ws.wv.as<T>(), *y = ws.yv.as<T>(), *B = ws.binv.as<T>();
+  T *w = ws.wv.as<T>(), *y = ws.yv.as<T>(), *B = out.as<T>();
   for (int c = 0; c < m->n_node_colours; ++c) {
     int64_t b = m->node_colour_start[c], e = m->node_colour_start[c + 1];
     for (int f = 0; f < nf; ++f) {
@@ -182,8 +185,8 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
 // Schmidt (classical, applied twice), norms and the basis V in double; the
 // preconditioned directions Z and J.z in precision T.
 template <typename T>
-chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const double *b, double *x,
-                   const chns_solver_opts &o, int *its_out, Timer &tj, cudaStream_t st) {
+chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, const double *b,
+                   double *x, const chns_solver_opts &o, int *its_out, Timer &tj, cudaStream_t st) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
@@ -201,7 +204,6 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>(), *hp = ws.hpinned;
   double *h1 = hd, *h2 = hd + (kMaxRestart + 8), *nr = hd + 2 * (kMaxRestart + 8);
   double *cz = hd + 3 * (kMaxRestart + 8);
-  const T *Binv = ws.binv.as<T>();
 
   CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
   CHNS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -293,18 +295,40 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   return check_launch();
 }
 
-template <typename T>
+// An FP32-Krylov Newton iteration must cut ||F|| by at least this factor;
+// otherwise the rest of the step uses FP64 J.w (FP64 finish).
+constexpr double kFp32MinReduction = 10.0;
+
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char *e = std::getenv("CHNS_TRACE");
+    on = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
+
+// Newton on F(U; U_n) = 0 (Sec. 3.5).  FP64 residual and update; each
+// correction by FGMRES in the element precision.  With CHNS_FP32_BULK the
+// correction uses FP32 J.w and an FP32 block-Jacobi until an iteration fails
+// to cut ||F|| by kFp32MinReduction (the FP32 operator cannot resolve the
+// weakly stabilised pressure modes below that level); the remaining
+// iterations use FP64 J.w with the FP32 block-Jacobi promoted to FP64.
 chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_opts &o, const double *Un,
                         const double *Unm1, const double *forcing, const double *bc, double *U,
                         chns_step_stats *stats, cudaStream_t st) {
-  auto t0 = std::chrono::steady_clock::now();
   Workspace &ws = m->ws;
-  const int64_t n = m->n_nodes * m->nf;
+  const int nf = m->nf;
+  const int64_t n = m->n_nodes * nf;
+  const int64_t nb = m->n_nodes * nf * nf;
   PhysCoef pc = make_coef(*p, m->lo, m->hi);
   TRY(ws.F.ensure(sizeof(double) * n));
   TRY(ws.dU.ensure(sizeof(double) * n));
   double *F = ws.F.as<double>(), *dU = ws.dU.as<double>();
   Timer tj, tr, tp;  // accumulated J.w, residual and preconditioner times
+  const bool mixed = o.precision == CHNS_FP32_BULK;
+  bool use64 = !mixed;
+  bool have_pc = false, have_pc64 = false;
 
   if (Unm1) vec_lincomb(2.0, Un, -1.0, Unm1, U, n, st);
   else CHNS_CUDA_TRY(cudaMemcpyAsync(U, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -312,8 +336,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   double *ut = nullptr, *dl = nullptr;
   auto residual = [&](double *fn) -> chns_status {
     TRY(prepare<double>(m, U, Un, st, &ut, &dl));
-    cudaEvent_t e0 = nullptr;
-    if (stats) { TRY(ensure_events(ws, 64)); e0 = ws.ev[60]; CHNS_CUDA_TRY(cudaEventRecord(e0, st)); }
+    if (stats) { TRY(ensure_events(ws, 64)); CHNS_CUDA_TRY(cudaEventRecord(ws.ev[60], st)); }
     TRY(residual_prepared(m, pc, U, ut, dl, forcing, bc, F, st));
     if (stats) CHNS_CUDA_TRY(cudaEventRecord(ws.ev[61], st));
     TRY(norm2(m, F, fn, st));
@@ -329,34 +352,56 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   double fn = 0.0;
   TRY(residual(&fn));
   const double f0 = fn;
-  int its = 0, kits = 0;
-  bool have_pc = false;
+  int its = 0, kits = 0, its64 = 0;
   while (!(fn <= std::max(o.newton_rtol * f0, o.newton_atol))) {
     if (its >= o.newton_max_it) {
       set_error("Newton reached %d iterations with ||F|| = %.3e (start %.3e)", its, fn, f0);
-      if (stats) { stats->newton_its = its; stats->res_final = fn; }
+      if (stats) { stats->newton_its = its; stats->res_final = fn; stats->res0 = f0; }
       return CHNS_ERR_NEWTON;
     }
-    T *ut_t = nullptr, *dl_t = nullptr;
-    TRY(prepare<T>(m, U, Un, st, &ut_t, &dl_t));
-    if (!have_pc || !o.reuse_preconditioner) {
-      auto a = std::chrono::steady_clock::now();
-      TRY(build_block_jacobi<T>(m, pc, ut_t, dl_t, st));
-      tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-      have_pc = true;
-    }
-    vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
     int k = 0;
     Timer tk;  // event slots 0.. (the residual uses slots 60, 61)
     tk.ws = &ws;
     tk.on = stats != nullptr;
-    TRY(fgmres<T>(m, pc, ut_t, dl_t, F, dU, o, &k, tk, st));
+    vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
+    auto a = std::chrono::steady_clock::now();
+    if (!use64) {
+      float *ut_t = nullptr, *dl_t = nullptr;
+      TRY(prepare<float>(m, U, Un, st, &ut_t, &dl_t));
+      if (!have_pc || !o.reuse_preconditioner) {
+        TRY(build_block_jacobi<float>(m, pc, ut_t, dl_t, ws.binv, st));
+        have_pc = true;
+        tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+      }
+      TRY(fgmres<float>(m, pc, ut_t, dl_t, ws.binv.as<float>(), F, dU, o, &k, tk, st));
+    } else {
+      double *ut_t = nullptr, *dl_t = nullptr;
+      TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
+      if (mixed) {
+        if (!have_pc64) {  // promote the FP32 blocks
+          TRY(ws.binv64.ensure(sizeof(double) * nb));
+          vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
+          have_pc64 = true;
+        }
+      } else if (!have_pc || !o.reuse_preconditioner) {
+        TRY(build_block_jacobi<double>(m, pc, ut_t, dl_t, ws.binv64, st));
+        have_pc = true;
+        tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+      }
+      TRY(fgmres<double>(m, pc, ut_t, dl_t, ws.binv64.as<double>(), F, dU, o, &k, tk, st));
+      if (mixed) ++its64;
+    }
     tj.ms += tk.ms;
     tj.calls += tk.calls;
     kits += k;
     vec_axpby(1.0, dU, 1.0, U, n, st);
     ++its;
+    const double prev = fn;
     TRY(residual(&fn));
+    if (trace_on())
+      fprintf(stderr, "[chns] newton %d |F|/|F0| = %.3e krylov %d (%s J.w)\n", its, fn / f0, k,
+              use64 ? "fp64" : "fp32");
+    if (mixed && !use64 && fn * kFp32MinReduction > prev) use64 = true;
   }
   if (stats) {
     stats->newton_its = its;
@@ -368,8 +413,8 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     stats->residual_ms = tr.ms;
     stats->residual_calls = tr.calls;
     stats->precond_ms = tp.ms;
+    stats->fp64_newton_its = its64;
   }
-  (void)t0;
   return CHNS_OK;
 }
 
@@ -412,10 +457,8 @@ chns_status step_impl(chns_mesh *m, const chns_params *p, const chns_solver_opts
     stats->energy_old = em[0];
     stats->mass_old = em[1];
   }
-  if (o->precision == CHNS_FP64)
-    s = newton_step<double>(m, p, *o, U_n, U_nm1, forcing, bc, U_np1, stats, st);
-  else if (o->precision == CHNS_FP32_BULK)
-    s = newton_step<float>(m, p, *o, U_n, U_nm1, forcing, bc, U_np1, stats, st);
+  if (o->precision == CHNS_FP64 || o->precision == CHNS_FP32_BULK)
+    s = newton_step(m, p, *o, U_n, U_nm1, forcing, bc, U_np1, stats, st);
   else {
     set_error("unknown precision");
     return CHNS_ERR_ARG;
@@ -483,7 +526,7 @@ void chns_mesh_destroy(chns_mesh *m) {
   cudaFree(m->node_perm);
   m->ws.ut.release(); m->ws.dl.release(); m->ws.ut32.release(); m->ws.dl32.release(); m->ws.f.release();
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
-  m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.red.release(); m->ws.hdev.release();
+  m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
   delete m;
   cudaSetDevice(prev);
 }

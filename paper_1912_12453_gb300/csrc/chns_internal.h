@@ -53,7 +53,8 @@ struct Workspace {
   DevBuf V;                            // double (m+1) n_dof Krylov basis
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors
-  DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks
+  DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks (element precision)
+  DevBuf binv64;                       // the same blocks in double (FP64 J.w iterations)
   DevBuf red;                          // reduction partials
   DevBuf hdev;                         // device copy of Gram-Schmidt coefficients
   double *hpinned = nullptr;           // pinned host mirror of reduction results

@@ -136,7 +136,7 @@ def _inv_norm(J, seed=0, its=25):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["band2", "band3"])
+@pytest.mark.parametrize("name", ["band2", "front3"])
 def test_step_matches_oracle(pairs, name, precision):
     """One CN step from the droplet's initial state.
 
