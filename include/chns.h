@@ -174,6 +174,23 @@ chns_status chns_energy_mass(const chns_mesh *mesh, const chns_params *params,
                              const double *U, double *energy, double *mass,
                              double *bubble_mass, void *stream);
 
+/* Allocation-free variant of chns_energy_mass, for callers that may not
+ * allocate device memory while they run: work issued during a CUDA graph
+ * stream capture (cudaMalloc is refused there) and host frameworks that give
+ * all device memory to their own pool up front.  The paper has no
+ * counterpart; it computes the same three integrals as chns_energy_mass, in
+ * the same order.  out3: caller-owned DEVICE array of 3 doubles receiving
+ * (energy, integral of phi, volume with phi < 0); asynchronous on stream.
+ * The reduction scratch is a fixed 1.5 MiB array inside the library, held
+ * by every GPU that loads it until the process exits; meshes of more than
+ * 2,097,152 leaves in 3D (4,194,304 in 2D) are rejected with CHNS_ERR_ARG.
+ * The first call on each device looks up that array's device address; make
+ * it before any stream capture.  Calls that overlap on the GPU share the
+ * scratch and race; order them on one stream.  Never calls cudaMalloc or
+ * cudaFree. */
+chns_status chns_energy_mass_noalloc(const chns_mesh *mesh, const chns_params *params,
+                                     const double *U, double *out3, void *stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent problems (meshes of any size, own parameters) advanced

@@ -24,7 +24,7 @@ STATUS = {0: "CHNS_OK", 1: "CHNS_ERR_ARG", 2: "CHNS_ERR_MESH", 3: "CHNS_ERR_CUDA
 EXPORTS = ["chns_mesh_create", "chns_mesh_info", "chns_mesh_node_coords", "chns_mesh_destroy",
            "chns_residual", "chns_jacvec", "chns_init_mu", "chns_step", "chns_energy_mass",
            "chns_batch_create", "chns_batch_step", "chns_batch_destroy", "chns_last_error",
-           "chns_kernel_launches"]
+           "chns_kernel_launches", "chns_energy_mass_noalloc"]
 
 
 class ChnsError(RuntimeError):
@@ -105,6 +105,8 @@ def lib():
         L.chns_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.chns_energy_mass.restype = st
         L.chns_energy_mass.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.chns_energy_mass_noalloc.restype = st
+        L.chns_energy_mass_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.chns_batch_create.restype = st
         L.chns_batch_create.argtypes = [i32, vp, vp, ctypes.POINTER(vp)]
         L.chns_batch_step.restype = st
@@ -228,6 +230,14 @@ def energy_mass(mesh: Mesh, params, U, stream=None):
 
 def kernel_launches() -> int:
     return int(lib().chns_kernel_launches())
+
+
+def energy_mass_noalloc(mesh: Mesh, params, U, out3, stream=None):
+    """Allocation-free diagnostics: out3 is a CUDA float64 tensor of 3 entries."""
+    prm = Params.of(params)
+    _check(lib().chns_energy_mass_noalloc(mesh.handle, ctypes.byref(prm), _ptr(U), _ptr(out3),
+                                          _stream(stream)))
+    return out3
 
 
 class Batch:
