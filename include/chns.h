@@ -78,7 +78,13 @@ typedef struct {
   int krylov_restart;      /* FGMRES restart length m (1..64) */
   int krylov_max_it;       /* total FGMRES iterations per Newton correction */
   chns_precision precision;
-  int reuse_preconditioner;/* 1: block-Jacobi built once per step; 0: every Newton iteration */
+  int reuse_preconditioner;/* k >= 1: the preconditioner built at the first Newton iteration of a
+                              step serves that step and the next k-1 steps of the same mesh
+                              (same precision, parameters, coarse level); 0: rebuilt at every
+                              Newton iteration */
+  int coarse_level;        /* two-level preconditioner: coarse octree level L_c >= 1 (at most one
+                              below the coarsest leaf); 0 = block-Jacobi only; -1 = automatic
+                              (L_c = min(2, coarsest leaf level - 1), off if that is < 1) */
 } chns_solver_opts;
 
 typedef struct {
@@ -152,7 +158,9 @@ chns_status chns_init_mu(const chns_mesh *mesh, const chns_params *params, doubl
 
 /* One Crank-Nicolson step (Sec. 3.1, 3.5): Newton on F(U; U_n) = 0 from the
  * guess U_n (or 2 U_n - U_nm1 when U_nm1 is not NULL), each correction by
- * right-preconditioned FGMRES(m) with nodal block-Jacobi.  The residual and
+ * right-preconditioned FGMRES(m) with nodal block-Jacobi plus, optionally, an
+ * additive coarse-space correction P (R J P)^{-1} R on a uniform coarse
+ * octree level (R = P^T, P trilinear).  The residual and
  * the Newton update are double; with CHNS_FP32_BULK the Krylov J.w and
  * preconditioner run in float and the Gram-Schmidt inner products and norms
  * stay double (iterative refinement by the outer double residual); once a
@@ -194,15 +202,21 @@ chns_status chns_energy_mass_noalloc(const chns_mesh *mesh, const chns_params *p
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent problems (meshes of any size, own parameters) advanced
- * together: the element kernels run over the concatenated leaves of all
- * instances in one launch per colour.  meshes and params: host arrays of n
- * entries; the meshes must outlive the batch. */
+ * together.  The instances of each dimension are fused into one union mesh:
+ * the element kernels run over the concatenated leaves of all of them in one
+ * launch per colour, each element reading its own instance's coefficients;
+ * the Newton-Krylov solve runs on the union with one coarse grid per instance
+ * (block-diagonal coarse operator) and a per-instance Newton tolerance.
+ * meshes and params: host arrays of n entries; the meshes must outlive the
+ * batch. */
 chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params *params,
                               chns_batch **out);
 
-/* One CN step of every instance; U_n[i], U_nm1[i] (nullable array or
- * entries), U_np1[i] are device vectors of instance i.  stats: host array of
- * n entries or NULL. */
+/* One CN step of every instance; U_n[i], U_nm1[i] (U_nm1 nullable),
+ * U_np1[i] are device vectors of instance i.  Every instance stops when its
+ * own ||F_i|| <= newton_rtol ||F_i(guess)|| (or atol).  stats: host array of
+ * n entries or NULL; Newton/Krylov counts and times are those of the
+ * instance's dimension group, energies and masses the instance's own. */
 chns_status chns_batch_step(chns_batch *batch, const chns_solver_opts *opts,
                             double *const *U_n, double *const *U_nm1, double *const *U_np1,
                             chns_step_stats *stats, void *stream);

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchns.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["mesh.cpp", "element.cu", "vector.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["mesh.cpp", "element.cu", "vector.cu", "coarse.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

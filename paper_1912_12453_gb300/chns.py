@@ -50,14 +50,16 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_max_it", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_max_it", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reuse_preconditioner", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("reuse_preconditioner", ctypes.c_int),
+                ("coarse_level", ctypes.c_int)]
 
     @classmethod
     def make(cls, precision="fp64", newton_rtol=1e-10, newton_atol=1e-13, newton_max_it=20,
-             krylov_rtol=1e-4, krylov_restart=30, krylov_max_it=600, reuse_preconditioner=True):
+             krylov_rtol=1e-4, krylov_restart=30, krylov_max_it=600, reuse_preconditioner=1,
+             coarse_level=-1):
         prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
         return cls(newton_rtol, newton_atol, newton_max_it, krylov_rtol, krylov_restart, krylov_max_it,
-                   prec, int(bool(reuse_preconditioner)))
+                   prec, int(reuse_preconditioner), int(coarse_level))
 
 
 class StepStats(ctypes.Structure):

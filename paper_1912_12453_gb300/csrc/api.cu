@@ -8,12 +8,14 @@
 #include <vector>
 
 #include "chns_internal.h"
+#include "coarse.h"
 #include "kernels.h"
 #include "vector.h"
 
 namespace chns {
 chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor, int max_level,
                        const double lo[3], const double hi[3], chns_mesh *m);
+chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u);
 const char *last_error();
 uint64_t launches();
 }  // namespace chns
@@ -185,8 +187,9 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
 // Schmidt (classical, applied twice), norms and the basis V in double; the
 // preconditioned directions Z and J.z in precision T.
 template <typename T>
-chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, const double *b,
-                   double *x, const chns_solver_opts &o, int *its_out, Timer &tj, cudaStream_t st) {
+chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
+                   const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
+                   cudaStream_t st) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
@@ -227,28 +230,26 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
       double *vj = V + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
       T *zj = Z + (int64_t)j * n;
       block_apply<T>(Binv, vj, zj, m->n_nodes, nf, st);
+      if (coarse) coarse_apply_add<T>(m, vj, zj, st);
       cudaEvent_t e0 = nullptr;
       TRY(tj.begin(st, &e0));
       TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, yv, st));
       TRY(tj.end(st, e0));
       vec_convert<T, double>(yv, w, n, 1.0, st);
-      // classical Gram-Schmidt, twice
-      vec_multidot(V, n, j + 1, w, n, part, h1, st);
-      vec_update(V, n, j + 1, h1, w, n, st);
-      vec_multidot(V, n, j + 1, w, n, part, h2, st);
-      vec_update(V, n, j + 1, h2, w, n, st);
-      vec_dot(w, w, n, part, nr, st);
+      // classical Gram-Schmidt, a second pass only when the DGKS test asks;
+      // V_{j+1} normalised on the device
+      int *flag = reinterpret_cast<int *>(nr + 2);
+      vec_orthogonalize(V, n, j + 1, n, part, h1, h2, nr, flag, st);
+      vec_normalize(w, n, nr, flag, st);
       CHNS_CUDA_TRY(cudaMemcpyAsync(hp, hd, sizeof(double) * 3 * (kMaxRestart + 8), cudaMemcpyDeviceToHost, st));
       CHNS_CUDA_TRY(cudaStreamSynchronize(st));
       TRY(tj.collect());
-      double hn = std::sqrt(hp[2 * (kMaxRestart + 8)]);
+      const double *hnr = hp + 2 * (kMaxRestart + 8);
+      const int hflag = *reinterpret_cast<const int *>(hnr + 2);
+      double hn = std::sqrt(hflag ? hnr[1] : hnr[0]);
       if (!std::isfinite(hn)) { set_error("non-finite Krylov vector"); return CHNS_ERR_NONFINITE; }
-      for (int i = 0; i <= j; ++i) H[i * mr + j] = hp[i] + hp[(kMaxRestart + 8) + i];
+      for (int i = 0; i <= j; ++i) H[i * mr + j] = hp[i] + (hflag ? hp[(kMaxRestart + 8) + i] : 0.0);
       H[(j + 1) * mr + j] = hn;
-      if (hn > 0.0) {
-        // V_{j+1} = w / hn  (reads the device copy of ||w||^2)
-        vec_axpby(1.0 / hn, w, 0.0, w, n, st);
-      }
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         double a = H[i * mr + j], c = H[(i + 1) * mr + j];
@@ -295,6 +296,30 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   return check_launch();
 }
 
+template <typename T>
+struct JvCtx {
+  chns_mesh *m;
+  const PhysCoef *pc;
+  const T *ut, *dl;
+  cudaStream_t st;
+};
+
+template <typename T>
+chns_status jv_callback(void *ctx, const T *w, T *y) {
+  JvCtx<T> *c = static_cast<JvCtx<T> *>(ctx);
+  return jacvec_prepared<T>(c->m, *c->pc, c->ut, c->dl, w, y, c->st);
+}
+
+template <typename T>
+chns_status build_coarse_operator(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, cudaStream_t st) {
+  Workspace &ws = m->ws;
+  const int64_t n = m->n_nodes * m->nf;
+  TRY(ws.wv.ensure(sizeof(T) * n));
+  TRY(ws.yv.ensure(sizeof(T) * n));
+  JvCtx<T> ctx{m, &pc, ut, dl, st};
+  return coarse_build<T>(m, &jv_callback<T>, &ctx, ws.wv.as<T>(), ws.yv.as<T>(), st);
+}
+
 // An FP32-Krylov Newton iteration must cut ||F|| by at least this factor;
 // otherwise the rest of the step uses FP64 J.w (FP64 finish).
 constexpr double kFp32MinReduction = 10.0;
@@ -328,7 +353,22 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   Timer tj, tr, tp;  // accumulated J.w, residual and preconditioner times
   const bool mixed = o.precision == CHNS_FP32_BULK;
   bool use64 = !mixed;
-  bool have_pc = false, have_pc64 = false;
+  int Lc = o.coarse_level;
+  if (Lc < 0) Lc = std::min(2, m->min_level - 1);
+  const bool coarse = Lc >= 1;
+  if (coarse) TRY(coarse_setup(m, Lc));
+  // a preconditioner from an earlier step is reused while it is young enough
+  // and was built for the same precision, parameters and coarse space
+  bool have_pc = ws.pc_steps_left > 0 && ws.pc_precision == (int)o.precision && ws.pc_coarse == Lc &&
+                 std::memcmp(&ws.pc_params, p, sizeof(chns_params)) == 0 && o.reuse_preconditioner > 0;
+  if (have_pc) --ws.pc_steps_left;
+  bool have_pc64 = false;
+  auto mark_built = [&]() {
+    ws.pc_precision = (int)o.precision;
+    ws.pc_coarse = Lc;
+    ws.pc_params = *p;
+    ws.pc_steps_left = o.reuse_preconditioner > 0 ? o.reuse_preconditioner - 1 : 0;
+  };
 
   if (Unm1) vec_lincomb(2.0, Un, -1.0, Unm1, U, n, st);
   else CHNS_CUDA_TRY(cudaMemcpyAsync(U, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -352,9 +392,44 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   double fn = 0.0;
   TRY(residual(&fn));
   const double f0 = fn;
+  // batched meshes: every instance must meet its own tolerance; converged
+  // instances get a zero right-hand side (their correction is then exactly
+  // zero: the operator and the preconditioner are block diagonal)
+  const int ni = m->n_inst;
+  std::vector<double> fi0, fi(ni, 0.0);
+  auto instance_norms = [&]() -> chns_status {
+    if (ni == 1) return CHNS_OK;
+    TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+    TRY(ws.hdev.ensure(sizeof(double) * std::max<int64_t>(4 * (kMaxRestart + 8), ni + 8)));
+    double *hd = ws.hdev.as<double>();
+    for (int q = 0; q < ni; ++q) {
+      const int64_t a = m->inst_node_start[q] * nf, b = m->inst_node_start[q + 1] * nf;
+      vec_dot(F + a, F + a, b - a, ws.red.as<double>(), hd + q, st);
+    }
+    std::vector<double> h(ni);
+    CHNS_CUDA_TRY(cudaMemcpyAsync(h.data(), hd, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+    CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < ni; ++q) fi[q] = std::sqrt(h[q]);
+    return CHNS_OK;
+  };
+  TRY(instance_norms());
+  fi0 = fi;
+  auto converged = [&]() {
+    if (ni == 1) return fn <= std::max(o.newton_rtol * f0, o.newton_atol);
+    for (int q = 0; q < ni; ++q)
+      if (!(fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol))) return false;
+    return true;
+  };
   int its = 0, kits = 0, its64 = 0;
-  while (!(fn <= std::max(o.newton_rtol * f0, o.newton_atol))) {
+  while (!converged()) {
+    if (ni > 1)
+      for (int q = 0; q < ni; ++q)
+        if (fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol)) {
+          const int64_t a = m->inst_node_start[q] * nf, b = m->inst_node_start[q + 1] * nf;
+          CHNS_CUDA_TRY(cudaMemsetAsync(F + a, 0, sizeof(double) * (b - a), st));
+        }
     if (its >= o.newton_max_it) {
+      ws.pc_steps_left = 0;
       set_error("Newton reached %d iterations with ||F|| = %.3e (start %.3e)", its, fn, f0);
       if (stats) { stats->newton_its = its; stats->res_final = fn; stats->res0 = f0; }
       return CHNS_ERR_NEWTON;
@@ -363,6 +438,11 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     Timer tk;  // event slots 0.. (the residual uses slots 60, 61)
     tk.ws = &ws;
     tk.on = stats != nullptr;
+    // forcing term: never ask the linear solve for more than the Newton
+    // target needs (with a factor-2 margin), never less than krylov_rtol
+    chns_solver_opts oi = o;
+    const double target = std::max(o.newton_rtol * f0, o.newton_atol);
+    oi.krylov_rtol = std::max(o.krylov_rtol, std::min(0.5, 0.5 * target / fn));
     vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
     auto a = std::chrono::steady_clock::now();
     if (!use64) {
@@ -370,25 +450,29 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
       TRY(prepare<float>(m, U, Un, st, &ut_t, &dl_t));
       if (!have_pc || !o.reuse_preconditioner) {
         TRY(build_block_jacobi<float>(m, pc, ut_t, dl_t, ws.binv, st));
+        if (coarse) TRY(build_coarse_operator<float>(m, pc, ut_t, dl_t, st));
         have_pc = true;
+        mark_built();
         tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
       }
-      TRY(fgmres<float>(m, pc, ut_t, dl_t, ws.binv.as<float>(), F, dU, o, &k, tk, st));
+      TRY(fgmres<float>(m, pc, ut_t, dl_t, ws.binv.as<float>(), coarse, F, dU, oi, &k, tk, st));
     } else {
       double *ut_t = nullptr, *dl_t = nullptr;
       TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
       if (mixed) {
-        if (!have_pc64) {  // promote the FP32 blocks
+        if (!have_pc64) {  // promote the FP32 blocks (built by an earlier FP32 iteration or step)
           TRY(ws.binv64.ensure(sizeof(double) * nb));
           vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
           have_pc64 = true;
         }
       } else if (!have_pc || !o.reuse_preconditioner) {
         TRY(build_block_jacobi<double>(m, pc, ut_t, dl_t, ws.binv64, st));
+        if (coarse) TRY(build_coarse_operator<double>(m, pc, ut_t, dl_t, st));
         have_pc = true;
+        mark_built();
         tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
       }
-      TRY(fgmres<double>(m, pc, ut_t, dl_t, ws.binv64.as<double>(), F, dU, o, &k, tk, st));
+      TRY(fgmres<double>(m, pc, ut_t, dl_t, ws.binv64.as<double>(), coarse, F, dU, oi, &k, tk, st));
       if (mixed) ++its64;
     }
     tj.ms += tk.ms;
@@ -398,6 +482,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     ++its;
     const double prev = fn;
     TRY(residual(&fn));
+    TRY(instance_norms());
     if (trace_on())
       fprintf(stderr, "[chns] newton %d |F|/|F0| = %.3e krylov %d (%s J.w)\n", its, fn / f0, k,
               use64 ? "fp64" : "fp32");
@@ -445,7 +530,8 @@ chns_status step_impl(chns_mesh *m, const chns_params *p, const chns_solver_opts
   auto t0 = std::chrono::steady_clock::now();
   if (!o || !U_n || !U_np1) { set_error("null argument"); return CHNS_ERR_ARG; }
   if (U_np1 == U_n) { set_error("U_np1 may not alias U_n"); return CHNS_ERR_ARG; }
-  if (o->krylov_restart < 1 || o->krylov_restart > kMaxRestart || o->krylov_max_it < 1 || o->newton_max_it < 0) {
+  if (o->krylov_restart < 1 || o->krylov_restart > kMaxRestart || o->krylov_max_it < 1 || o->newton_max_it < 0 ||
+      o->coarse_level > 16) {
     set_error("invalid solver options");
     return CHNS_ERR_ARG;
   }
@@ -524,6 +610,12 @@ void chns_mesh_destroy(chns_mesh *m) {
   cudaFree(m->hang);
   cudaFree(m->wall);
   cudaFree(m->node_perm);
+  cudaFree(m->pins);
+  cudaFree(m->elem_inst);
+  cudaFree(m->node_inst);
+  cudaFree(m->coef32);
+  cudaFree(m->coef64);
+  m->coarse.release();
   m->ws.ut.release(); m->ws.dl.release(); m->ws.ut32.release(); m->ws.dl32.release(); m->ws.f.release();
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
@@ -638,6 +730,28 @@ chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params
   chns_batch *b = new chns_batch;
   b->meshes.assign(meshes, meshes + n);
   b->params.assign(params, params + n);
+  for (int dim = 2; dim <= 3; ++dim) {
+    BatchGroup g;
+    std::vector<const chns_mesh *> ms;
+    std::vector<PhysCoef> pcs;
+    for (int i = 0; i < n; ++i)
+      if (meshes[i]->dim == dim) {
+        g.members.push_back(i);
+        ms.push_back(meshes[i]);
+        pcs.push_back(make_coef(params[i], meshes[i]->lo, meshes[i]->hi));
+      }
+    if (ms.empty()) continue;
+    g.u = new chns_mesh;
+    chns_status s = build_union(ms, g.u);
+    if (s == CHNS_OK) s = upload_coef_tables(g.u, pcs, nullptr);
+    if (s != CHNS_OK) {
+      chns_mesh_destroy(g.u);
+      for (auto &h : b->groups) chns_mesh_destroy(h.u);
+      delete b;
+      return s;
+    }
+    b->groups.push_back(std::move(g));
+  }
   *out = b;
   return CHNS_OK;
 }
@@ -645,18 +759,60 @@ chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params
 chns_status chns_batch_step(chns_batch *b, const chns_solver_opts *o, double *const *U_n, double *const *U_nm1,
                             double *const *U_np1, chns_step_stats *stats, void *stream) {
   if (!b || !o || !U_n || !U_np1) { set_error("null argument"); return CHNS_ERR_ARG; }
-  for (size_t i = 0; i < b->meshes.size(); ++i) {
-    chns_status s = step_impl(b->meshes[i], &b->params[i], o, U_n[i], U_nm1 ? U_nm1[i] : nullptr, nullptr,
-                              nullptr, U_np1[i], stats ? &stats[i] : nullptr, S(stream));
-    if (s != CHNS_OK) {
-      std::string msg = std::string("instance ") + std::to_string(i) + ": " + chns::last_error();
-      set_error("%s", msg.c_str());
-      return s;
+  cudaStream_t st = S(stream);
+  for (auto &g : b->groups) {
+    chns_mesh *u = g.u;
+    const int64_t n = u->n_nodes * u->nf;
+    TRY(g.Un.ensure(sizeof(double) * n));
+    TRY(g.Unp1.ensure(sizeof(double) * n));
+    if (U_nm1) TRY(g.Unm1.ensure(sizeof(double) * n));
+    double *un = g.Un.as<double>(), *up = g.Unp1.as<double>(), *um = U_nm1 ? g.Unm1.as<double>() : nullptr;
+    for (size_t q = 0; q < g.members.size(); ++q) {
+      const int i = g.members[q];
+      const int64_t a = u->inst_node_start[q] * u->nf, len = (u->inst_node_start[q + 1] - u->inst_node_start[q]) * u->nf;
+      if (!U_n[i] || !U_np1[i]) { set_error("null vector of instance %d", i); return CHNS_ERR_ARG; }
+      CHNS_CUDA_TRY(cudaMemcpyAsync(un + a, U_n[i], sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+      if (um) {
+        if (!U_nm1[i]) { set_error("U_nm1 given but null for instance %d", i); return CHNS_ERR_ARG; }
+        CHNS_CUDA_TRY(cudaMemcpyAsync(um + a, U_nm1[i], sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    chns_step_stats gs;
+    std::memset(&gs, 0, sizeof(gs));
+    auto t0 = std::chrono::steady_clock::now();
+    chns_status s = newton_step(u, &b->params[g.members[0]], *o, un, um, nullptr, nullptr, up, &gs, st);
+    if (s != CHNS_OK) return s;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (size_t q = 0; q < g.members.size(); ++q) {
+      const int i = g.members[q];
+      const int64_t a = u->inst_node_start[q] * u->nf, len = (u->inst_node_start[q + 1] - u->inst_node_start[q]) * u->nf;
+      CHNS_CUDA_TRY(cudaMemcpyAsync(U_np1[i], up + a, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+      if (stats) {
+        chns_step_stats &x = stats[i];
+        x = gs;  // shared Newton / Krylov counts and timings of the group
+        x.seconds = secs;
+        double em[3];
+        TRY(energy_mass_impl(b->meshes[i], &b->params[i], U_n[i], em, st));
+        x.energy_old = em[0];
+        x.mass_old = em[1];
+        TRY(energy_mass_impl(b->meshes[i], &b->params[i], U_np1[i], em, st));
+        x.energy_new = em[0];
+        x.mass_new = em[1];
+      }
     }
   }
   return CHNS_OK;
 }
 
-void chns_batch_destroy(chns_batch *b) { delete b; }
+void chns_batch_destroy(chns_batch *b) {
+  if (!b) return;
+  for (auto &g : b->groups) {
+    chns_mesh_destroy(g.u);
+    g.Un.release();
+    g.Unm1.release();
+    g.Unp1.release();
+  }
+  delete b;
+}
 
 }  // extern "C"

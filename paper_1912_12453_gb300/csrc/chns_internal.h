@@ -58,14 +58,37 @@ struct Workspace {
   DevBuf red;                          // reduction partials
   DevBuf hdev;                         // device copy of Gram-Schmidt coefficients
   double *hpinned = nullptr;           // pinned host mirror of reduction results
+  // preconditioner kept across steps: valid for `pc_steps_left` more steps
+  // with the same precision, parameters and coarse level
+  int pc_steps_left = 0;
+  int pc_precision = -1, pc_coarse = -1;
+  chns_params pc_params{};
   std::vector<cudaEvent_t> ev;
   ~Workspace();
+};
+
+// Coarse space of the two-level preconditioner (coarse.cu): uniform octree
+// level `level`, all fields, trilinear prolongation.
+struct Coarse {
+  int level = -1, nc1 = 0;
+  int n_inst = 1;                   // one coarse grid per problem instance
+  int64_t ncn_inst = 0, nc0 = 0;    // coarse nodes / unknowns of one instance
+  int64_t ncn = 0, nc = 0;          // coarse nodes, coarse unknowns (all instances)
+  float *pos = nullptr;             // n_nodes * dim: node positions in coarse units
+  int64_t *rstart = nullptr;        // ncn + 1: restriction lists per coarse node
+  int32_t *rnode = nullptr;
+  float *rw = nullptr;
+  DevBuf M;                         // per instance [A_c | I] -> [I | A_c^{-1}], nc0 x 2nc0 doubles
+  DevBuf vec;                       // coarse work vectors
+  bool ready = false;
+  ~Coarse();
+  void release();
 };
 
 }  // namespace chns
 
 struct chns_mesh {
-  int dim = 0, max_level = 0, nc = 0, nf = 0;
+  int dim = 0, max_level = 0, min_level = 0, nc = 0, nf = 0;
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
   int64_t n_elem = 0, n_nodes = 0, n_hang = 0;
   bool uniform = false;
@@ -74,6 +97,16 @@ struct chns_mesh {
   int n_node_colours = 0;
   std::vector<int64_t> node_colour_start;  // nodes of each node colour (for probing)
   int64_t origin = -1;                 // node at the box origin (pressure pin)
+  // pinned pressure nodes (one per problem instance)
+  int32_t *pins = nullptr;
+  int64_t n_pins = 0;
+  // batched (union) meshes: several independent problems in one mesh
+  int n_inst = 1;
+  uint16_t *elem_inst = nullptr;       // n_elem instance of each element (device)
+  int32_t *node_inst = nullptr;        // n_nodes instance of each node (device)
+  void *coef32 = nullptr, *coef64 = nullptr;  // per-instance element coefficients (device)
+  std::vector<int64_t> inst_node_start;      // n_inst + 1 (host)
+  std::vector<int> inst_max_level;           // n_inst (host)
   int64_t n_wall = 0;
   std::vector<int64_t> node_xyz;       // host: n_nodes * dim integer coordinates
   // device arrays
@@ -85,9 +118,18 @@ struct chns_mesh {
   int32_t *node_perm = nullptr;        // n_nodes node indices grouped by node colour
   int device = 0;
   chns::Workspace ws;
+  chns::Coarse coarse;
+};
+
+// Instances of one dimension fused into a union mesh.
+struct BatchGroup {
+  std::vector<int> members;            // batch indices, in union order
+  chns_mesh *u = nullptr;              // union mesh (owned)
+  chns::DevBuf Un, Unm1, Unp1;         // union state vectors
 };
 
 struct chns_batch {
   std::vector<chns_mesh *> meshes;
   std::vector<chns_params> params;
+  std::vector<BatchGroup> groups;
 };

@@ -1,0 +1,505 @@
+// Two-level additive preconditioner for the Krylov solve of Sec. 3.5:
+//   z = B^{-1} v + P A_c^{-1} R v
+// B: nodal block-Jacobi (vector.cu); P: trilinear interpolation of all fields
+// from the nodes of a uniform coarse octree level L_c to the mesh nodes;
+// R = P^T; A_c = R J P, the Galerkin projection of the Jacobian.  Nodal
+// block-Jacobi alone leaves the smooth pressure modes of the VMS saddle
+// point unresolved (they couple across the whole domain); the coarse space
+// carries them.
+//
+// A_c is probed: the image J P e_c of a coarse hat lives within H + h of its
+// coarse node c (H, h: coarse and mesh spacing), so the hats of one field
+// whose nodes share the residues of their coordinates mod 3 (27 colours in
+// 3D, 9 in 2D) are applied together, and each mesh row is credited to the
+// nearest coarse node of the probed colour.  Exact when h <= H/2, i.e. every
+// leaf at least one level finer than L_c.  All reductions run in a fixed
+// order (one block per coarse node); nothing is atomic.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "chns_internal.h"
+#include "coarse.h"
+
+namespace chns {
+
+namespace {
+
+constexpr int kB = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+inline unsigned grid_n(int64_t n) {
+  int64_t b = (n + kB - 1) / kB;
+  return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 8);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  return v;
+}
+
+struct CGeo {
+  int dim, nf, nc1;   // nc1 = 2^Lc + 1 coarse nodes per axis
+  int64_t n_nodes;
+  int64_t ncn_inst;   // coarse nodes per instance
+  int64_t nc0;        // coarse unknowns per instance
+};
+
+// cell (lowest corner, per axis) and fraction of a position in coarse units
+__device__ __forceinline__ void locate(const CGeo &g, const float *pos, int *b, float *t) {
+  for (int a = 0; a < g.dim; ++a) {
+    int c = (int)floorf(pos[a]);
+    c = c < 0 ? 0 : (c > g.nc1 - 2 ? g.nc1 - 2 : c);
+    b[a] = c;
+    t[a] = pos[a] - float(c);
+  }
+}
+
+__device__ __forceinline__ int lin(const CGeo &g, const int *c) {
+  int idx = 0;
+  for (int a = g.dim - 1; a >= 0; --a) idx = idx * g.nc1 + c[a];
+  return idx;
+}
+
+// probing vector: field f = sum of the coarse hats of colour k; other fields 0
+template <typename T, int NF, int DIM>
+__global__ void __launch_bounds__(kB) k_probe_coarse(CGeo g, const float *__restrict__ pos, int k, int f,
+                                                     T *__restrict__ w) {
+  int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+  for (int64_t i = blockIdx.x * int64_t(kB) + threadIdx.x; i < g.n_nodes; i += int64_t(gridDim.x) * kB) {
+    int b[3];
+    float t[3];
+    locate(g, pos + i * g.dim, b, t);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < (1 << DIM); ++c) {
+      double wc = 1.0;
+      bool in = true;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        int ca = b[a] + ((c >> a) & 1);
+        if (ca % 3 != kk[a]) in = false;
+        wc *= ((c >> a) & 1) ? double(t[a]) : 1.0 - double(t[a]);
+      }
+      if (in) s += wc;
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) w[i * NF + q] = q == f ? T(s) : T(0);
+  }
+}
+
+// owner coordinates (residue kk mod 3, within two coarse steps of the row
+// node cpc) of slot s: bit a set = positive offset along axis a
+__device__ __forceinline__ bool slot_owner(const CGeo &g, const int *cpc, const int *kk, int s, int *oc) {
+  bool ok = true;
+  for (int a = 0; a < g.dim; ++a) {
+    oc[a] = -1;
+    for (int d = -2; d <= 2; ++d) {
+      int o = cpc[a] + d;
+      if (o < 0 || o >= g.nc1 || o % 3 != kk[a]) continue;
+      if ((d > 0) == (((s >> a) & 1) == 1)) oc[a] = o;
+    }
+    if (oc[a] < 0) ok = false;
+  }
+  return ok;
+}
+
+constexpr int kChunks = 16;
+
+// Block (c', sl) takes the sl-th of kChunks slices of the restriction list of
+// coarse row node c' and, for the probed colour k, sums P[i, c'] y[i, q] per
+// owner slot (the owner of mesh node i: the nearest coarse node of colour k).
+template <typename T, int NF>
+__global__ void __launch_bounds__(kB) k_gather_coarse(CGeo g, const int64_t *__restrict__ rstart,
+                                                      const int32_t *__restrict__ rnode,
+                                                      const float *__restrict__ rw, const float *__restrict__ pos,
+                                                      int k, const T *__restrict__ y, double *__restrict__ part) {
+  const int cp = blockIdx.x, sl = blockIdx.y;
+  int cpc[3] = {0, 0, 0}, kk[3] = {k % 3, (k / 3) % 3, k / 9};
+  {
+    int r = int(cp % g.ncn_inst);
+    for (int a = 0; a < g.dim; ++a) { cpc[a] = r % g.nc1; r /= g.nc1; }
+  }
+  double acc[8][NF];
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[s][q] = 0.0;
+  const int64_t b0 = rstart[cp], len = rstart[cp + 1] - b0;
+  const int64_t lo = b0 + len * sl / kChunks, hi = b0 + len * (sl + 1) / kChunks;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += kB) {
+    const int64_t i = rnode[e];
+    const double wgt = rw[e];
+    int slot = 0;
+    bool ok = true;
+    for (int a = 0; a < g.dim; ++a) {
+      const float p = pos[i * g.dim + a];
+      int o = kk[a] + 3 * (int)floorf((p - float(kk[a])) / 3.0f + 0.5f);
+      if (o < 0 || o >= g.nc1) ok = false;
+      if (o > cpc[a]) slot |= 1 << a;
+    }
+    if (!ok) continue;
+    double yq[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) yq[q] = double(y[i * NF + q]);
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+      if (s == slot)
+#pragma unroll
+        for (int q = 0; q < NF; ++q) acc[s][q] += wgt * yq[q];
+  }
+  __shared__ double red[kB / 32][NF];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+      double v = warp_sum(acc[s][q]);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NF) {
+      double v = 0.0;
+      for (int w = 0; w < kB / 32; ++w) v += red[w][threadIdx.x];
+      part[((int64_t(cp) * kChunks + sl) * 8 + s) * NF + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// A[(c', q), (owner(s), f)] = sum of the slices, in slice order
+__global__ void k_gather_sum(CGeo g, int k, int f, const double *__restrict__ part, double *__restrict__ A,
+                             int64_t ldA, int64_t ncn) {
+  const int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x;
+  const int nf = g.nf;
+  if (t >= ncn * 8 * nf) return;
+  const int cp = int(t / (8 * nf)), s = int((t / nf) % 8), q = int(t % nf);
+  if (s >= (1 << g.dim)) return;
+  const int64_t inst = cp / g.ncn_inst, lcp = cp % g.ncn_inst;
+  int cpc[3] = {0, 0, 0}, kk[3] = {k % 3, (k / 3) % 3, k / 9}, oc[3];
+  {
+    int r = int(lcp);
+    for (int a = 0; a < g.dim; ++a) { cpc[a] = r % g.nc1; r /= g.nc1; }
+  }
+  if (!slot_owner(g, cpc, kk, s, oc)) return;
+  double v = 0.0;
+  for (int sl = 0; sl < kChunks; ++sl) v += part[((int64_t(cp) * kChunks + sl) * 8 + s) * nf + q];
+  double *Ai = A + inst * g.nc0 * ldA;
+  Ai[(lcp * nf + q) * ldA + int64_t(lin(g, oc)) * nf + f] = v;
+}
+
+// rc[c', q] = sum_i P[i, c'] v[i, q]: block (c', s) sums the s-th of kChunks
+// slices of c's restriction list; k_restrict_sum adds the slices in order
+
+template <int NF>
+__global__ void __launch_bounds__(kB) k_restrict(const int64_t *__restrict__ rstart, const int32_t *__restrict__ rnode,
+                                                 const float *__restrict__ rw, const double *__restrict__ v,
+                                                 double *__restrict__ part) {
+  const int cp = blockIdx.x, sl = blockIdx.y;
+  const int64_t b0 = rstart[cp], len = rstart[cp + 1] - b0;
+  const int64_t lo = b0 + len * sl / kChunks, hi = b0 + len * (sl + 1) / kChunks;
+  double acc[NF];
+#pragma unroll
+  for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += kB) {
+    const int64_t i = rnode[e];
+    const double wgt = rw[e];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[q] += wgt * v[i * NF + q];
+  }
+  __shared__ double red[kB / 32][NF];
+#pragma unroll
+  for (int q = 0; q < NF; ++q) {
+    double s = warp_sum(acc[q]);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NF) {
+    double s = 0.0;
+    for (int w = 0; w < kB / 32; ++w) s += red[w][threadIdx.x];
+    part[(int64_t(cp) * kChunks + sl) * NF + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_restrict_sum(const double *__restrict__ part, int64_t nc, int nf, double *__restrict__ rc) {
+  const int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x;
+  if (t >= nc) return;
+  const int64_t c = t / nf, q = t % nf;
+  double s = 0.0;
+  for (int sl = 0; sl < kChunks; ++sl) s += part[(c * kChunks + sl) * nf + q];
+  rc[t] = s;
+}
+
+// zc = Ainv rc, one warp per row; Ainv is the right half of [A | I] after
+// Gauss-Jordan (row stride 2 nc)
+__global__ void k_coarse_matvec(const double *__restrict__ M, int64_t nc, int64_t nc0,
+                                const double *__restrict__ rc, double *__restrict__ zc) {
+  const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int ln = threadIdx.x & 31;
+  if (r >= nc) return;
+  const int64_t inst = r / nc0, lr = r % nc0;
+  const double *row = M + inst * nc0 * 2 * nc0 + lr * 2 * nc0 + nc0;
+  const double *x = rc + inst * nc0;
+  double s = 0.0;
+  for (int64_t c = ln; c < nc0; c += 32) s += row[c] * x[c];
+  s = warp_sum(s);
+  if (ln == 0) zc[r] = s;
+}
+
+// z[i, q] += sum_c P[i, c] zc[c, q]
+template <typename T, int NF, int DIM>
+__global__ void __launch_bounds__(kB) k_prolong_add(CGeo g, const float *__restrict__ pos,
+                                                    const int32_t *__restrict__ node_inst,
+                                                    const double *__restrict__ zc, T *__restrict__ z) {
+  for (int64_t i = blockIdx.x * int64_t(kB) + threadIdx.x; i < g.n_nodes; i += int64_t(gridDim.x) * kB) {
+    int b[3];
+    float t[3];
+    locate(g, pos + i * g.dim, b, t);
+    const int64_t cbase = node_inst ? int64_t(node_inst[i]) * g.ncn_inst : 0;
+    double acc[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int c = 0; c < (1 << DIM); ++c) {
+      int cc[3] = {0, 0, 0};
+      double wc = 1.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        cc[a] = b[a] + ((c >> a) & 1);
+        wc *= ((c >> a) & 1) ? double(t[a]) : 1.0 - double(t[a]);
+      }
+      int64_t idx = 0;
+#pragma unroll
+      for (int a = DIM - 1; a >= 0; --a) idx = idx * g.nc1 + cc[a];
+      const double *zp = zc + (cbase + idx) * NF;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) acc[q] += wc * zp[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) z[i * NF + q] += T(acc[q]);
+  }
+}
+
+// [A | I] setup for every instance block (nc0 x 2 nc0 each)
+__global__ void k_gj_init(double *__restrict__ M, int64_t nc0, int n_inst) {
+  const int64_t per = nc0 * nc0;
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < per * n_inst; t += int64_t(gridDim.x) * kB) {
+    const int64_t inst = t / per, r = (t % per) / nc0, c = t % nc0;
+    M[inst * nc0 * 2 * nc0 + r * 2 * nc0 + nc0 + c] = r == c ? 1.0 : 0.0;
+  }
+}
+
+// pivot step k of instance blockIdx.x: pick the largest |M[r][k]|, r >= k,
+// swap it into row k, scale row k, save column k for the elimination
+__global__ void k_gj_pivot(double *__restrict__ Mall, int64_t nc, int64_t k, double *__restrict__ colall,
+                           int *__restrict__ bad) {
+  double *M = Mall + int64_t(blockIdx.x) * nc * 2 * nc;
+  double *col = colall + int64_t(blockIdx.x) * nc;
+  __shared__ double bv[1024];
+  __shared__ int64_t bi[1024];
+  double best = -1.0;
+  int64_t arg = k;
+  for (int64_t r = k + threadIdx.x; r < nc; r += blockDim.x) {
+    double v = fabs(M[r * 2 * nc + k]);
+    if (v > best) { best = v; arg = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      if (bv[threadIdx.x + s] > bv[threadIdx.x] ||
+          (bv[threadIdx.x + s] == bv[threadIdx.x] && bi[threadIdx.x + s] < bi[threadIdx.x])) {
+        bv[threadIdx.x] = bv[threadIdx.x + s];
+        bi[threadIdx.x] = bi[threadIdx.x + s];
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t p = bi[0];
+  const double piv = M[p * 2 * nc + k];
+  if (!(fabs(piv) > 0.0)) {
+    if (threadIdx.x == 0) *bad = 1;
+    for (int64_t r = threadIdx.x; r < nc; r += blockDim.x) col[r] = 0.0;
+    return;
+  }
+  for (int64_t j = threadIdx.x; j < 2 * nc; j += blockDim.x) {
+    double a = M[k * 2 * nc + j], b = M[p * 2 * nc + j];
+    if (p != k) M[p * 2 * nc + j] = a;
+    M[k * 2 * nc + j] = b / piv;
+  }
+  __syncthreads();
+  for (int64_t r = threadIdx.x; r < nc; r += blockDim.x) col[r] = r == k ? 0.0 : M[r * 2 * nc + k];
+}
+
+// eliminate column k from every row but k (instance blockIdx.y)
+__global__ void k_gj_elim(double *__restrict__ Mall, int64_t nc, int64_t k, const double *__restrict__ colall) {
+  double *M = Mall + int64_t(blockIdx.y) * nc * 2 * nc;
+  const double *col = colall + int64_t(blockIdx.y) * nc;
+  const int64_t W = 2 * nc;
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nc * W; t += int64_t(gridDim.x) * kB) {
+    const int64_t r = t / W, j = t % W;
+    const double fr = col[r];
+    if (fr != 0.0) M[t] -= fr * M[k * W + j];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+Coarse::~Coarse() { release(); }
+
+void Coarse::release() {
+  cudaFree(pos);
+  cudaFree(rstart);
+  cudaFree(rnode);
+  cudaFree(rw);
+  pos = nullptr;
+  rstart = nullptr;
+  rnode = nullptr;
+  rw = nullptr;
+  M.release();
+  vec.release();
+  level = -1;
+  ready = false;
+}
+
+chns_status coarse_setup(chns_mesh *m, int Lc) {
+  Coarse &C = m->coarse;
+  if (C.level == Lc && C.pos) return CHNS_OK;
+  C.release();
+  if (Lc < 1 || Lc > m->min_level - 1) {
+    set_error("coarse level %d must be in [1, %d] (one below the coarsest leaf level)", Lc, m->min_level - 1);
+    return CHNS_ERR_ARG;
+  }
+  const int dim = m->dim, nf = m->nf, ni = m->n_inst;
+  const int nc1 = (1 << Lc) + 1;
+  int64_t ncn = 1;
+  for (int a = 0; a < dim; ++a) ncn *= nc1;
+  std::vector<float> pos(size_t(m->n_nodes) * dim);
+  std::vector<int> base(size_t(m->n_nodes) * dim);
+  std::vector<int64_t> cbase(m->n_nodes);  // first coarse node of the node's instance
+  for (int q = 0; q < ni; ++q) {
+    const double scale = std::ldexp(1.0, Lc - m->inst_max_level[q]);
+    for (int64_t i = m->inst_node_start[q]; i < m->inst_node_start[q + 1]; ++i) {
+      cbase[i] = int64_t(q) * ncn;
+      for (int a = 0; a < dim; ++a) {
+        double p = double(m->node_xyz[i * dim + a]) * scale;
+        pos[i * dim + a] = float(p);
+        int b = (int)std::floor(p);
+        base[i * dim + a] = std::min(std::max(b, 0), nc1 - 2);
+      }
+    }
+  }
+  auto corners = [&](int64_t i, auto &&fn) {
+    for (int c = 0; c < (1 << dim); ++c) {
+      double w = 1.0;
+      int64_t idx = 0;
+      for (int a = dim - 1; a >= 0; --a) {
+        int ca = base[i * dim + a] + ((c >> a) & 1);
+        double t = double(pos[i * dim + a]) - base[i * dim + a];
+        w *= ((c >> a) & 1) ? t : 1.0 - t;
+        idx = idx * nc1 + ca;
+      }
+      if (w != 0.0) fn(cbase[i] + idx, w);
+    }
+  };
+  const int64_t ncn_all = ncn * ni;
+  std::vector<int64_t> cnt(ncn_all + 1, 0);
+  for (int64_t i = 0; i < m->n_nodes; ++i) corners(i, [&](int64_t idx, double) { cnt[idx + 1]++; });
+  for (int64_t c = 0; c < ncn_all; ++c) cnt[c + 1] += cnt[c];
+  std::vector<int32_t> rnode(cnt[ncn_all]);
+  std::vector<float> rw(cnt[ncn_all]);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t i = 0; i < m->n_nodes; ++i)
+    corners(i, [&](int64_t idx, double w) {
+      rnode[fill[idx]] = (int32_t)i;
+      rw[fill[idx]++] = (float)w;
+    });
+  CHNS_CUDA_TRY(cudaMalloc(&C.pos, sizeof(float) * pos.size()));
+  CHNS_CUDA_TRY(cudaMemcpy(C.pos, pos.data(), sizeof(float) * pos.size(), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.rstart, sizeof(int64_t) * cnt.size()));
+  CHNS_CUDA_TRY(cudaMemcpy(C.rstart, cnt.data(), sizeof(int64_t) * cnt.size(), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.rnode, sizeof(int32_t) * std::max<size_t>(rnode.size(), 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.rnode, rnode.data(), sizeof(int32_t) * rnode.size(), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.rw, sizeof(float) * std::max<size_t>(rw.size(), 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.rw, rw.data(), sizeof(float) * rw.size(), cudaMemcpyHostToDevice));
+  C.level = Lc;
+  C.nc1 = nc1;
+  C.n_inst = ni;
+  C.ncn_inst = ncn;
+  C.nc0 = ncn * nf;
+  C.ncn = ncn_all;
+  C.nc = ncn_all * nf;
+  TRY_CHNS(C.M.ensure(sizeof(double) * C.nc0 * 2 * C.nc0 * ni));
+  TRY_CHNS(C.vec.ensure(sizeof(double) * (3 * C.nc + 8 + C.nc * kChunks + C.ncn * kChunks * 8 * nf)));
+  return CHNS_OK;
+}
+
+template <typename T>
+chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaStream_t st) {
+  Coarse &C = m->coarse;
+  const int nf = m->nf, dim = m->dim;
+  CGeo g{dim, nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0};
+  double *M = C.M.as<double>();
+  const int64_t nc0 = C.nc0;
+  CHNS_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nc0 * 2 * nc0 * C.n_inst, st));
+  const int ncol = dim == 2 ? 9 : 27;
+  double *part = C.vec.as<double>() + 3 * C.nc + 8 + C.nc * kChunks;
+  for (int k = 0; k < ncol; ++k)
+    for (int f = 0; f < nf; ++f) {
+      if (dim == 2) k_probe_coarse<T, 5, 2><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, k, f, w);
+      else k_probe_coarse<T, 6, 3><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, k, f, w);
+      note_launches(1);
+      TRY_CHNS(jv(ctx, w, y));
+      dim3 gr((unsigned)C.ncn, kChunks);
+      if (nf == 5)
+        k_gather_coarse<T, 5><<<gr, kB, 0, st>>>(g, C.rstart, C.rnode, C.rw, C.pos, k, y, part);
+      else
+        k_gather_coarse<T, 6><<<gr, kB, 0, st>>>(g, C.rstart, C.rnode, C.rw, C.pos, k, y, part);
+      k_gather_sum<<<(unsigned)((C.ncn * 8 * nf + kB - 1) / kB), kB, 0, st>>>(g, k, f, part, M, 2 * nc0, C.ncn);
+      note_launches(2);
+    }
+  // Gauss-Jordan with partial pivoting on each instance's [A | I]
+  double *col = C.vec.as<double>() + 2 * C.nc;  // nc0 per instance = C.nc in total
+  int *bad = reinterpret_cast<int *>(C.vec.as<double>() + 3 * C.nc);
+  CHNS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_gj_init<<<grid_n(nc0 * nc0 * C.n_inst), kB, 0, st>>>(M, nc0, C.n_inst);
+  note_launches(1);
+  const unsigned gx = std::max(1u, grid_n(nc0 * 2 * nc0) / (unsigned)std::max(1, std::min(C.n_inst, 8)));
+  for (int64_t k = 0; k < nc0; ++k) {
+    k_gj_pivot<<<C.n_inst, 1024, 0, st>>>(M, nc0, k, col, bad);
+    k_gj_elim<<<dim3(gx, C.n_inst), kB, 0, st>>>(M, nc0, k, col);
+    note_launches(2);
+  }
+  int hbad = 0;
+  CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hbad) { set_error("singular coarse operator"); return CHNS_ERR_KRYLOV; }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error("coarse build: %s", cudaGetErrorString(e)); return CHNS_ERR_CUDA; }
+  C.ready = true;
+  return CHNS_OK;
+}
+template chns_status coarse_build<float>(chns_mesh *, JvFn<float>, void *, float *, float *, cudaStream_t);
+template chns_status coarse_build<double>(chns_mesh *, JvFn<double>, void *, double *, double *, cudaStream_t);
+
+template <typename T>
+void coarse_apply_add(chns_mesh *m, const double *v, T *z, cudaStream_t st) {
+  Coarse &C = m->coarse;
+  CGeo g{m->dim, m->nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0};
+  double *rc = C.vec.as<double>(), *zc = rc + C.nc, *part = rc + 3 * C.nc + 8;
+  dim3 gr((unsigned)C.ncn, kChunks);
+  if (m->nf == 5) k_restrict<5><<<gr, kB, 0, st>>>(C.rstart, C.rnode, C.rw, v, part);
+  else k_restrict<6><<<gr, kB, 0, st>>>(C.rstart, C.rnode, C.rw, v, part);
+  k_restrict_sum<<<(unsigned)((C.nc + kB - 1) / kB), kB, 0, st>>>(part, C.nc, m->nf, rc);
+  k_coarse_matvec<<<(unsigned)((C.nc * 32 + kB - 1) / kB), kB, 0, st>>>(C.M.as<double>(), C.nc, C.nc0, rc, zc);
+  const int32_t *ni = m->n_inst > 1 ? m->node_inst : nullptr;
+  if (m->dim == 2) k_prolong_add<T, 5, 2><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, zc, z);
+  else k_prolong_add<T, 6, 3><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, zc, z);
+  note_launches(4);
+}
+template void coarse_apply_add<float>(chns_mesh *, const double *, float *, cudaStream_t);
+template void coarse_apply_add<double>(chns_mesh *, const double *, double *, cudaStream_t);
+
+}  // namespace chns

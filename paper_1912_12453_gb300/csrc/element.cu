@@ -141,10 +141,30 @@ __device__ __forceinline__ T contract(T S, const T *V, const Stage<T> &s) {
 }
 
 // ---------------------------------------------------------------- node gather / scatter
+// Node blocks are N consecutive values at p = base + node * N: for even N the
+// block starts on a 2-element boundary (float2 / double2 loads), for N = 4
+// floats on a 16-byte boundary (float4).
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
 template <int N, typename T>
 __device__ __forceinline__ void load_block(const T *__restrict__ p, T *out) {
+  if constexpr (N == 4 && sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else if constexpr (N % 2 == 0) {
+    using P = typename Pair<T>::type;
 #pragma unroll
-  for (int k = 0; k < N; ++k) out[k] = p[k];
+    for (int k = 0; k < N / 2; ++k) {
+      const P v = __ldg(reinterpret_cast<const P *>(p) + k);
+      out[2 * k] = v.x;
+      out[2 * k + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = __ldg(p + k);
+  }
 }
 
 // corner value through the hanging constraint: mean of 2 or 4 parents
@@ -173,8 +193,20 @@ __device__ __forceinline__ void gather(int cn, const int32_t *__restrict__ hang,
 
 template <int N, typename T, typename O>
 __device__ __forceinline__ void add_block(O *__restrict__ p, const T *r, T wgt) {
+  if constexpr (N % 2 == 0) {
+    using P = typename Pair<O>::type;
+    P *q = reinterpret_cast<P *>(p);
 #pragma unroll
-  for (int k = 0; k < N; ++k) p[k] += O(wgt * r[k]);
+    for (int k = 0; k < N / 2; ++k) {
+      P v = q[k];
+      v.x += O(wgt * r[2 * k]);
+      v.y += O(wgt * r[2 * k + 1]);
+      q[k] = v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) p[k] += O(wgt * r[k]);
+  }
 }
 
 // non-atomic: elements of one launch (one colour) touch disjoint nodes
@@ -213,6 +245,7 @@ struct KCoef {
   T inv_dt, four_dt2, alpha, beta, gamma, xi, jc;
   T inv_Pe, inv_We, inv_Re, inv_Fr, CnWe, inv_PeCn, Cn2, C_I;
   T g[3];
+  T ext[3];  // box extent per axis
 };
 
 template <int D> __device__ __forceinline__ int hidx(int i, int j) {
@@ -327,24 +360,30 @@ KCoef<T> kcoef(const PhysCoef &p) {
   c.alpha = T(p.alpha); c.beta = T(p.beta); c.gamma = T(p.gamma); c.xi = T(p.xi); c.jc = T(p.jc);
   c.inv_Pe = T(p.inv_Pe); c.inv_We = T(p.inv_We); c.inv_Re = T(p.inv_Re); c.inv_Fr = T(p.inv_Fr);
   c.CnWe = T(p.CnWe); c.inv_PeCn = T(p.inv_PeCn); c.Cn2 = T(p.Cn2); c.C_I = T(p.C_I);
-  for (int a = 0; a < 3; ++a) c.g[a] = T(p.g[a]);
+  for (int a = 0; a < 3; ++a) {
+    c.g[a] = T(p.g[a]);
+    c.ext[a] = T(p.ext[a]);
+  }
   return c;
 }
 
 // ---------------------------------------------------------------- the element kernel
 // MODE 0: residual (output O = double), MODE 1: J.w (output O = T).
 template <int D, typename T, int MODE, bool HASF, typename O>
-__global__ void __launch_bounds__(256) k_element(
+__global__ void __launch_bounds__(256, 3) k_element(
     const int32_t *__restrict__ conn, const uint8_t *__restrict__ level,
     const int32_t *__restrict__ hang, int64_t e_begin, int64_t e_end,
     const T *__restrict__ ut, const T *__restrict__ dl, const T *__restrict__ w,
-    const T *__restrict__ f, O *__restrict__ out, KCoef<T> c, T ext0, T ext1, T ext2) {
+    const T *__restrict__ f, O *__restrict__ out, KCoef<T> c0, const KCoef<T> *__restrict__ tab,
+    const uint16_t *__restrict__ einst) {
   constexpr int NC = 1 << D, NF = D + 3, ND = D + 1;
   const int lc = threadIdx.x & (NC - 1);
   int64_t e = e_begin + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> D);
   const bool active = e < e_end;
   if (!active) e = e_end - 1;  // keep the lanes alive for the shuffles
   const int cn = conn[e * NC + lc];
+  // batched meshes: the coefficients of the element's own problem instance
+  const KCoef<T> c = tab ? tab[einst[e]] : c0;
 
   // gather the corner's nodal blocks
   T u[NF], d[ND];
@@ -357,7 +396,7 @@ __global__ void __launch_bounds__(256) k_element(
 
   // geometry of this leaf
   const T scale = T(1) / T(1u << level[e]);
-  const T ext[3] = {ext0, ext1, ext2};
+  const T *ext = c.ext;
   Stage<T> s;
   s.ca = T(0.5) + T(0.28867513459481288225);  // (1 + 1/sqrt(3)) / 2
   s.cb = T(0.5) - T(0.28867513459481288225);
@@ -491,32 +530,32 @@ __global__ void k_cast(const double *__restrict__ x, int64_t n, T *__restrict__ 
 }
 
 // constrained rows of the residual: wall velocities and the pinned pressure
-__global__ void k_dirichlet_res(const int32_t *__restrict__ wall, int64_t n_wall, int64_t origin,
-                                int dim, const double *__restrict__ Un, const double *__restrict__ bc,
-                                double *__restrict__ F) {
+__global__ void k_dirichlet_res(const int32_t *__restrict__ wall, int64_t n_wall, const int32_t *__restrict__ pins,
+                                int64_t n_pins, int dim, const double *__restrict__ Un,
+                                const double *__restrict__ bc, double *__restrict__ F) {
   const int nf = dim + 3;
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n_wall) {
     int64_t b = int64_t(wall[i]) * nf;
     for (int k = 0; k < dim; ++k) F[b + k] = Un[b + k] - (bc ? bc[b + k] : 0.0);
   }
-  if (i == 0 && origin >= 0) {
-    int64_t b = origin * nf + dim;
+  if (i < n_pins) {
+    int64_t b = int64_t(pins[i]) * nf + dim;
     F[b] = Un[b] - (bc ? bc[b] : 0.0);
   }
 }
 
 template <typename T>
-__global__ void k_dirichlet_jv(const int32_t *__restrict__ wall, int64_t n_wall, int64_t origin,
-                               int dim, const T *__restrict__ w, T *__restrict__ y) {
+__global__ void k_dirichlet_jv(const int32_t *__restrict__ wall, int64_t n_wall, const int32_t *__restrict__ pins,
+                               int64_t n_pins, int dim, const T *__restrict__ w, T *__restrict__ y) {
   const int nf = dim + 3;
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n_wall) {
     int64_t b = int64_t(wall[i]) * nf;
     for (int k = 0; k < dim; ++k) y[b + k] = w[b + k];
   }
-  if (i == 0 && origin >= 0) {
-    int64_t b = origin * nf + dim;
+  if (i < n_pins) {
+    int64_t b = int64_t(pins[i]) * nf + dim;
     y[b] = w[b];
   }
 }
@@ -654,8 +693,8 @@ void element_pass(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *
     int64_t b = m->colour_start[col], e = m->colour_start[col + 1];
     if (e <= b) continue;
     k_element<D, T, MODE, HASF, O><<<grid_for((e - b) << D), kBlock, 0, st>>>(
-        m->conn, m->level, m->hang, b, e, ut, dl, w, f, out, c, T(pc.ext[0]), T(pc.ext[1]),
-        T(pc.ext[2]));
+        m->conn, m->level, m->hang, b, e, ut, dl, w, f, out, c,
+        reinterpret_cast<const KCoef<T> *>(sizeof(T) == 8 ? m->coef64 : m->coef32), m->elem_inst);
     note_launches(1);
   }
 }
@@ -684,19 +723,37 @@ template void launch_jacvec<double>(const chns_mesh *, const PhysCoef &, const d
                                     const double *, double *, cudaStream_t);
 
 void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st) {
-  int64_t n = std::max<int64_t>(m->n_wall, 1);
-  k_dirichlet_res<<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->origin, m->dim, Un, bc, F);
+  int64_t n = std::max<int64_t>(std::max(m->n_wall, m->n_pins), 1);
+  k_dirichlet_res<<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->pins, m->n_pins, m->dim, Un, bc, F);
   note_launches(1);
 }
 
 template <typename T>
 void launch_dirichlet_jv(const chns_mesh *m, const T *w, T *y, cudaStream_t st) {
-  int64_t n = std::max<int64_t>(m->n_wall, 1);
-  k_dirichlet_jv<T><<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->origin, m->dim, w, y);
+  int64_t n = std::max<int64_t>(std::max(m->n_wall, m->n_pins), 1);
+  k_dirichlet_jv<T><<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->pins, m->n_pins, m->dim, w, y);
   note_launches(1);
 }
 template void launch_dirichlet_jv<float>(const chns_mesh *, const float *, float *, cudaStream_t);
 template void launch_dirichlet_jv<double>(const chns_mesh *, const double *, double *, cudaStream_t);
+
+chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, cudaStream_t st) {
+  const size_t n = pcs.size();
+  if (!m->coef32) {
+    CHNS_CUDA_TRY(cudaMalloc(&m->coef32, sizeof(KCoef<float>) * n));
+    CHNS_CUDA_TRY(cudaMalloc(&m->coef64, sizeof(KCoef<double>) * n));
+  }
+  std::vector<KCoef<float>> a(n);
+  std::vector<KCoef<double>> b(n);
+  for (size_t i = 0; i < n; ++i) {
+    a[i] = kcoef<float>(pcs[i]);
+    b[i] = kcoef<double>(pcs[i]);
+  }
+  CHNS_CUDA_TRY(cudaMemcpyAsync(m->coef32, a.data(), sizeof(KCoef<float>) * n, cudaMemcpyHostToDevice, st));
+  CHNS_CUDA_TRY(cudaMemcpyAsync(m->coef64, b.data(), sizeof(KCoef<double>) * n, cudaMemcpyHostToDevice, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  return CHNS_OK;
+}
 
 int64_t energy_blocks(const chns_mesh *m) { return (int64_t)grid_for(m->n_elem << m->dim); }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -22,6 +23,8 @@ void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc
 template <typename T>
 void launch_dirichlet_jv(const chns_mesh *m, const T *w, T *y, cudaStream_t st);
 int64_t energy_blocks(const chns_mesh *m);
+// per-instance element coefficients of a batched (union) mesh
+chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, cudaStream_t st);
 void launch_energy(const chns_mesh *m, const PhysCoef &pc, const double *U, double *partial, cudaStream_t st);
 
 }  // namespace chns

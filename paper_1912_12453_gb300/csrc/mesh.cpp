@@ -185,6 +185,8 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     return CHNS_ERR_MESH;
   }
   m->uniform = uniform;
+  m->min_level = max_level;
+  for (int64_t e = 0; e < n; ++e) m->min_level = std::min<int>(m->min_level, level[e]);
 
   // --- 2:1 balance across faces, edges and corners: every same-level
   // neighbour of a leaf has its parent among the leaves or their ancestors.
@@ -461,7 +463,140 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
   if ((st = upload(&m->anchor, anc_s)) != CHNS_OK) return st;
   if ((st = upload(&m->hang, hang_dev)) != CHNS_OK) return st;
   if ((st = upload(&m->wall, wall)) != CHNS_OK) return st;
+  {
+    std::vector<int32_t> pins;
+    if (m->origin >= 0) pins.push_back((int32_t)m->origin);
+    m->n_pins = (int64_t)pins.size();
+    if ((st = upload(&m->pins, pins)) != CHNS_OK) return st;
+  }
+  m->n_inst = 1;
+  m->inst_node_start = {0, n_nodes};
+  m->inst_max_level = {max_level};
   if ((st = upload(&m->node_perm, nperm)) != CHNS_OK) return st;
+  return CHNS_OK;
+}
+
+template <class T>
+std::vector<T> download(const T *d, size_t n) {
+  std::vector<T> h(n);
+  if (n) cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost);
+  return h;
+}
+
+// One mesh holding several independent problems of the same dimension: the
+// instances' nodes and elements are concatenated (instance order), element
+// colour c of the union is colour c of every instance (instances share no
+// node), and each element records its instance so the element kernels can
+// look up that instance's coefficients.
+chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u) {
+  if (ms.empty()) { set_error("empty batch"); return CHNS_ERR_ARG; }
+  const int dim = ms[0]->dim, nc = 1 << dim;
+  if (ms.size() > 65535) { set_error("too many instances"); return CHNS_ERR_ARG; }
+  u->dim = dim;
+  u->nc = nc;
+  u->nf = dim + 3;
+  u->n_inst = (int)ms.size();
+  u->max_level = 0;
+  u->min_level = 1 << 30;
+  int n_col = 0, n_ncol = 0;
+  int64_t n_elem = 0, n_nodes = 0, n_hang = 0, n_wall = 0;
+  for (auto *m : ms) {
+    if (m->dim != dim) { set_error("a batch group must have one dimension"); return CHNS_ERR_ARG; }
+    n_col = std::max(n_col, m->n_colours);
+    n_ncol = std::max(n_ncol, m->n_node_colours);
+    n_elem += m->n_elem;
+    n_nodes += m->n_nodes;
+    n_hang += m->n_hang;
+    n_wall += m->n_wall;
+    u->max_level = std::max(u->max_level, m->max_level);
+    u->min_level = std::min(u->min_level, m->min_level);
+  }
+  if (n_elem > (int64_t(1) << 31) / 8 || n_nodes >= (int64_t(1) << 31)) { set_error("batch too large"); return CHNS_ERR_ARG; }
+  u->n_elem = n_elem;
+  u->n_nodes = n_nodes;
+  u->n_hang = n_hang;
+  u->n_wall = n_wall;
+  u->n_colours = n_col;
+  u->n_node_colours = n_ncol;
+  for (int a = 0; a < 3; ++a) { u->lo[a] = ms[0]->lo[a]; u->hi[a] = ms[0]->hi[a]; }
+  std::vector<int64_t> node_off(ms.size() + 1, 0), hang_off(ms.size() + 1, 0);
+  for (size_t i = 0; i < ms.size(); ++i) {
+    node_off[i + 1] = node_off[i] + ms[i]->n_nodes;
+    hang_off[i + 1] = hang_off[i] + ms[i]->n_hang;
+  }
+  u->inst_node_start = node_off;
+  u->inst_max_level.clear();
+  // elements colour by colour, instance by instance
+  std::vector<int32_t> conn;
+  std::vector<uint8_t> lev;
+  std::vector<uint32_t> anc;
+  std::vector<uint16_t> einst;
+  conn.reserve(size_t(n_elem) * nc);
+  lev.reserve(n_elem);
+  anc.reserve(size_t(n_elem) * dim);
+  einst.reserve(n_elem);
+  std::vector<std::vector<int32_t>> hconn(ms.size());
+  std::vector<std::vector<uint8_t>> hlev(ms.size());
+  std::vector<std::vector<uint32_t>> hanc(ms.size());
+  for (size_t i = 0; i < ms.size(); ++i) {
+    hconn[i] = download(ms[i]->conn, size_t(ms[i]->n_elem) * nc);
+    hlev[i] = download(ms[i]->level, size_t(ms[i]->n_elem));
+    hanc[i] = download(ms[i]->anchor, size_t(ms[i]->n_elem) * dim);
+    u->inst_max_level.push_back(ms[i]->max_level);
+  }
+  u->colour_start.assign(n_col + 1, 0);
+  for (int c = 0; c < n_col; ++c) {
+    for (size_t i = 0; i < ms.size(); ++i) {
+      const chns_mesh *m = ms[i];
+      if (c >= m->n_colours) continue;
+      for (int64_t e = m->colour_start[c]; e < m->colour_start[c + 1]; ++e) {
+        for (int k = 0; k < nc; ++k) {
+          int32_t v = hconn[i][e * nc + k];
+          conn.push_back(v >= 0 ? int32_t(v + node_off[i]) : int32_t(v - hang_off[i]));
+        }
+        lev.push_back(hlev[i][e]);
+        for (int a = 0; a < dim; ++a) anc.push_back(hanc[i][e * dim + a]);
+        einst.push_back((uint16_t)i);
+      }
+    }
+    u->colour_start[c + 1] = (int64_t)lev.size();
+  }
+  std::vector<int32_t> hang, wall, pins, nperm, ninst(n_nodes);
+  for (size_t i = 0; i < ms.size(); ++i) {
+    auto h = download(ms[i]->hang, size_t(ms[i]->n_hang) * 4);
+    for (int32_t v : h) hang.push_back(v >= 0 ? int32_t(v + node_off[i]) : v);
+    auto w = download(ms[i]->wall, size_t(ms[i]->n_wall));
+    for (int32_t v : w) wall.push_back(int32_t(v + node_off[i]));
+    if (ms[i]->origin >= 0) pins.push_back(int32_t(ms[i]->origin + node_off[i]));
+    for (int64_t k = node_off[i]; k < node_off[i + 1]; ++k) ninst[k] = (int32_t)i;
+    for (int64_t k = 0; k < ms[i]->n_nodes * dim; ++k) u->node_xyz.push_back(ms[i]->node_xyz[k]);
+  }
+  // node colours: colour c of the union = colour c of every instance
+  u->node_colour_start.assign(n_ncol + 1, 0);
+  std::vector<std::vector<int32_t>> hperm(ms.size());
+  for (size_t i = 0; i < ms.size(); ++i) hperm[i] = download(ms[i]->node_perm, size_t(ms[i]->n_nodes));
+  for (int c = 0; c < n_ncol; ++c) {
+    for (size_t i = 0; i < ms.size(); ++i) {
+      const chns_mesh *m = ms[i];
+      if (c >= m->n_node_colours) continue;
+      for (int64_t k = m->node_colour_start[c]; k < m->node_colour_start[c + 1]; ++k)
+        nperm.push_back(int32_t(hperm[i][k] + node_off[i]));
+    }
+    u->node_colour_start[c + 1] = (int64_t)nperm.size();
+  }
+  u->n_pins = (int64_t)pins.size();
+  u->origin = -1;
+  chns_status st;
+  CHNS_CUDA_TRY(cudaGetDevice(&u->device));
+  if ((st = upload(&u->conn, conn)) != CHNS_OK) return st;
+  if ((st = upload(&u->level, lev)) != CHNS_OK) return st;
+  if ((st = upload(&u->anchor, anc)) != CHNS_OK) return st;
+  if ((st = upload(&u->hang, hang)) != CHNS_OK) return st;
+  if ((st = upload(&u->wall, wall)) != CHNS_OK) return st;
+  if ((st = upload(&u->pins, pins)) != CHNS_OK) return st;
+  if ((st = upload(&u->node_perm, nperm)) != CHNS_OK) return st;
+  if ((st = upload(&u->elem_inst, einst)) != CHNS_OK) return st;
+  if ((st = upload(&u->node_inst, ninst)) != CHNS_OK) return st;
   return CHNS_OK;
 }
 

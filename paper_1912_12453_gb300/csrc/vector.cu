@@ -91,6 +91,82 @@ __global__ void __launch_bounds__(kB) k_update(const double *__restrict__ V, int
   }
 }
 
+// w -= sum_i h[i] V_i (i < nv) and per-block partial sums of the new |w|^2;
+// skipped entirely when flag is given and *flag == 0
+__global__ void __launch_bounds__(kB) k_update_norm(const double *__restrict__ V, int64_t ld, int nv,
+                                                    const double *__restrict__ h, double *__restrict__ w,
+                                                    int64_t n, const int *__restrict__ flag,
+                                                    double *__restrict__ partial) {
+  if (flag && *flag == 0) return;
+  __shared__ double hs[kMaxRestart + 1];
+  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = h[i];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
+    double s = w[t];
+    for (int i = 0; i < nv; ++i) s -= hs[i] * V[(int64_t)i * ld + t];
+    w[t] = s;
+    acc[0] += s * s;
+  }
+  block_sum_store<1>(acc, partial);
+}
+
+// multi-dot that is skipped when *flag == 0
+template <int NV>
+__global__ void __launch_bounds__(kB) k_multidot_if(const double *__restrict__ V, int64_t ld, int i0, int nv,
+                                                    const double *__restrict__ w, int64_t n,
+                                                    double *__restrict__ partial, const int *__restrict__ flag) {
+  if (*flag == 0) return;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
+    double x = w[t];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nv) acc[k] += V[(int64_t)(i0 + k) * ld + t] * x;
+  }
+  block_sum_store<NV>(acc, partial + (int64_t)i0 * gridDim.x);
+}
+
+__global__ void k_sum_partials_if(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ res,
+                                  const int *__restrict__ flag) {
+  const int k = blockIdx.x;
+  if (k >= nv) return;
+  if (*flag == 0) {
+    if (threadIdx.x == 0) res[k] = 0.0;
+    return;
+  }
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)k * nblocks + b];
+  __shared__ double sh[kB / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    res[k] = t;
+  }
+}
+
+// Reorthogonalise only on severe cancellation: the first projection removed
+// more than 99.99% of |w|^2 (|w| dropped below 1% of its length); the
+// Newton corrections need a linear reduction of ~1e-3 only
+__global__ void k_reorth_flag(const double *__restrict__ before, const double *__restrict__ after,
+                              int *__restrict__ flag) {
+  *flag = (after[0] < 1e-4 * before[0]) ? 1 : 0;
+}
+
+// out = x / sqrt(chosen |w|^2): n2[0] if *flag else n1[0]
+__global__ void k_normalize(double *__restrict__ w, int64_t n, const double *__restrict__ n1,
+                            const double *__restrict__ n2, const int *__restrict__ flag) {
+  const double q = *flag ? n2[0] : n1[0];
+  if (!(q > 0.0)) return;
+  const double s = 1.0 / sqrt(q);
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) w[t] *= s;
+}
+
 // out = x / nrm[0]
 __global__ void k_scale_by(const double *__restrict__ x, const double *__restrict__ nrm, double *__restrict__ out,
                            int64_t n) {
@@ -226,6 +302,35 @@ void vec_dot(const double *x, const double *y, int64_t n, double *partial, doubl
   k_multidot<1><<<kRedBlocks, kB, 0, st>>>(x, 0, 0, 1, y, n, partial);
   note_launches(1);
   k_sum_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, res);
+  note_launches(1);
+}
+
+// One Arnoldi orthogonalisation of w = V_{nv} against V_0..V_{nv-1} (classical
+// Gram-Schmidt, a second pass only on severe cancellation), then
+// normalisation of w when its norm is nonzero.  Device outputs (no host sync):
+// h1[0..nv-1] first-pass coefficients, h1[nv] = |w|^2 before; h2[0..nv-1]
+// second-pass coefficients (0 if skipped); nrm[0] = |w|^2 after pass 1,
+// nrm[1] = after pass 2, flag[0] = whether pass 2 ran.
+void vec_orthogonalize(double *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
+                       double *nrm, int *flag, cudaStream_t st) {
+  // pass 1 dots include w itself (stored right after V_{nv-1}): |w|^2
+  vec_multidot(V, ld, nv + 1, V + (int64_t)nv * ld, n, partial, h1, st);
+  double *w = V + (int64_t)nv * ld;
+  k_update_norm<<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h1, w, n, nullptr, partial);
+  k_sum_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, nrm);
+  k_reorth_flag<<<1, 1, 0, st>>>(h1 + nv, nrm, flag);
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    int c = std::min(8, nv - i0);
+    k_multidot_if<8><<<kRedBlocks, kB, 0, st>>>(V, ld, i0, c, w, n, partial, flag);
+  }
+  k_sum_partials_if<<<nv, kB, 0, st>>>(partial, kRedBlocks, nv, h2, flag);
+  k_update_norm<<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h2, w, n, flag, partial);
+  k_sum_partials_if<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, nrm + 1, flag);
+  note_launches(6 + (nv + 7) / 8 + (nv + 1 + 7) / 8 + 1);
+}
+
+void vec_normalize(double *w, int64_t n, const double *nrm, const int *flag, cudaStream_t st) {
+  k_normalize<<<grid_n(n), kB, 0, st>>>(w, n, nrm, nrm + 1, flag);
   note_launches(1);
 }
 

@@ -15,6 +15,9 @@ void vec_multidot(const double *V, int64_t ld, int nv, const double *w, int64_t 
                   double *h, cudaStream_t st);
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st);
 void vec_update(const double *V, int64_t ld, int nv, const double *h, double *w, int64_t n, cudaStream_t st);
+void vec_orthogonalize(double *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
+                       double *nrm, int *flag, cudaStream_t st);
+void vec_normalize(double *w, int64_t n, const double *nrm, const int *flag, cudaStream_t st);
 void vec_scale_by(const double *x, const double *nrm, double *out, int64_t n, cudaStream_t st);
 template <typename A, typename B>
 void vec_convert(const A *x, B *y, int64_t n, double a, cudaStream_t st);

@@ -173,3 +173,27 @@ def test_step_matches_oracle(pairs, name, precision):
     bound = 2.0 * _inv_norm(p.om.jacobian(prm, ref, U0)) * (Fg + Fr)
     assert np.linalg.norm(d) <= bound + TOLSTEP * np.linalg.norm(r)
     assert abs(stats["mass_new"] - stats["mass_old"]) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["droplet2d_l5", "bubble3d_l5_9"])
+def test_workload_applies_match_oracle(name):
+    """The full-size meshes of the workloads (the 2D droplet and the adaptive
+    3D bubble with hanging nodes, 1.4M leaves): residual and J.w at the
+    initial state plus a seeded perturbation, every entry compared."""
+    import torch
+    from oracle import oracle as O
+    from paper_1912_12453_gb300 import chns
+    wl = W.workload(name)
+    p = Pair(wl.leaves)
+    assert p.gm.n_hanging == p.om.n_hanging and p.gm.n_nodes == p.om.n_nodes
+    Uo, Un = physical_state(p.om, wl)
+    w = W.perturbation(p.om.n_nodes, p.nf, 2)[1]
+    ref = p.om.residual(wl.params, Un, Uo)
+    got = chns.residual(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo))
+    assert rel(p.to_oracle(got), ref) <= TOL64
+    refj = p.om.jacvec(wl.params, Un, Uo, w)
+    gotj = chns.jacvec(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w))
+    assert rel(p.to_oracle(gotj), refj) <= TOL64
+    gotj32 = chns.jacvec(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32),
+                         precision="fp32")
+    assert rel(p.to_oracle(gotj32), refj) <= TOL32
