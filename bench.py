@@ -37,10 +37,14 @@ from paper_1912_12453_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Jacobian-apply GDoF/s and s per CN step, FP32-mixed vs FP64 at equal residual"
 WORKLOAD = "droplet3d_l6"
-# FP32 operations per element of one J.w apply (3D), counted from the SASS
-# instruction mix of the element kernel under ncu: 2 x FFMA + FADD + FMUL +
-# transcendental/MUFU counted as 1 (see profiles/jacvec_fp32_droplet3d_l6.md).
-JV_FLOP_PER_ELEM_3D = None
+# FP32 operations per element of one 3D J.w apply, counted by ncu on the
+# element kernel (thread-level FADD + FMUL + 2 x FFMA, 3.547e8 per launch of
+# 32,768 elements; profiles/jacvec_fp32_droplet3d_l6.md).
+JV_FLOP_PER_ELEM_3D = 10825
+# DRAM bytes of one J.w apply (8 colour launches) of the level-6 droplet mesh,
+# read + write, from one ncu capture with --cache-control none after an L2
+# flush (same file).  Valid for the kernel as profiled; null for other meshes.
+JV_TRAFFIC_PER_APPLY = {262144: 15_311_872 + 37_344_768}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 HBM_PEAK_FALLBACK = 6800.0
 
@@ -350,8 +354,14 @@ def main():
     if JV_FLOP_PER_ELEM_3D:
         ach = JV_FLOP_PER_ELEM_3D * mesh.n_elem / (jv_apply_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_element<3,float,J.w>",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": JV_TRAFFIC_PER_APPLY.get(mesh.n_elem) if mesh.dim == 3 else None,
+                "per": f"one J.w apply ({mesh.n_colours} colour launches, {mesh.n_elem} elements, "
+                       f"{JV_FLOP_PER_ELEM_3D} flop/element)",
+                "kernel": "k_element<3,float,J.w>",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "hbm_gbs_achieved": (JV_TRAFFIC_PER_APPLY.get(mesh.n_elem, 0) / (jv_apply_ms / 1e3) / 1e9)
+                if mesh.dim == 3 else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
