@@ -190,6 +190,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="droplet3d_l6 (the metric's configuration), droplet2d_l5 or bubble3d_l5_9")
     ap.add_argument("--krylov-max-it", type=int, default=400)
+    ap.add_argument("--krylov-restart", type=int, default=64)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -261,10 +262,10 @@ def main():
 
     # ---- CN steps, FP32-bulk mixed (timed region)
     opts32 = chns.SolverOpts.make(precision="fp32", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
-                                  krylov_restart=30, krylov_max_it=args.krylov_max_it,
+                                  krylov_restart=args.krylov_restart, krylov_max_it=args.krylov_max_it,
                                   reuse_preconditioner=args.precond_steps)
     opts64 = chns.SolverOpts.make(precision="fp64", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
-                                  krylov_restart=30, krylov_max_it=args.krylov_max_it,
+                                  krylov_restart=args.krylov_restart, krylov_max_it=args.krylov_max_it,
                                   reuse_preconditioner=args.precond_steps)
     Ua = U0.clone()
     Ub = torch.empty_like(Ua)
@@ -379,6 +380,7 @@ def main():
                                    "1,647,750 DoF), Cn 0.02, Re 100, We 50, ratios 1e-2, dt 5e-4",
                        "precision": "FP32 element J.w + FP32 block-Jacobi inside FP64 Newton / FP64 Gram-Schmidt",
                        "newton_rtol": args.newton_rtol,
+                       "krylov": f"FGMRES({args.krylov_restart})",
                        "preconditioner": f"block-Jacobi + coarse level-2 Galerkin space, built once per {args.precond_steps} CN steps",
                        "l2": "step working set (Krylov basis 31 x 13 MB) > L2; apply sweep flushes L2",
                        "parallelism": f"replicas x{world}"},

@@ -55,7 +55,7 @@ class SolverOpts(ctypes.Structure):
 
     @classmethod
     def make(cls, precision="fp64", newton_rtol=1e-10, newton_atol=1e-13, newton_max_it=20,
-             krylov_rtol=1e-4, krylov_restart=30, krylov_max_it=600, reuse_preconditioner=1,
+             krylov_rtol=1e-4, krylov_restart=64, krylov_max_it=600, reuse_preconditioner=1,
              coarse_level=-1):
         prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
         return cls(newton_rtol, newton_atol, newton_max_it, krylov_rtol, krylov_restart, krylov_max_it,

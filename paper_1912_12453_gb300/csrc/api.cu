@@ -183,9 +183,11 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
 }
 
 // ---------------------------------------------------------------- FGMRES
-// Solve J x = b (b = -F) with right-preconditioned flexible GMRES(m); Gram-
-// Schmidt (classical, applied twice), norms and the basis V in double; the
-// preconditioned directions Z and J.z in precision T.
+// Solve J x = b (b = -F) with right-preconditioned flexible GMRES(m).  The
+// basis V, the preconditioned directions Z, J.z and the Gram-Schmidt
+// (classical, a second pass on severe cancellation) are in the element
+// precision T, with double accumulation of the dot products; the Hessenberg
+// least squares, x, r = b - J x and its norm are in double.
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
                    const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
@@ -194,16 +196,17 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
   const int mr = o.krylov_restart;
-  TRY(ws.V.ensure(sizeof(double) * (mr + 1) * n));
-  TRY(ws.Z.ensure(sizeof(T) * mr * n));
+  const int64_t ld = vec_ld(n);  // basis stride: 16-byte aligned vectors
+  TRY(ws.V.ensure(sizeof(T) * (mr + 1) * ld));
+  TRY(ws.Z.ensure(sizeof(T) * mr * ld));
   TRY(ws.r.ensure(sizeof(double) * n));
   TRY(ws.wv.ensure(sizeof(T) * n));
   TRY(ws.yv.ensure(sizeof(T) * n));
   TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
   TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
   TRY(ensure_pinned(ws));
-  double *V = ws.V.as<double>(), *r = ws.r.as<double>();
-  T *Z = ws.Z.as<T>(), *yv = ws.yv.as<T>(), *tv = ws.wv.as<T>();
+  double *r = ws.r.as<double>();
+  T *V = ws.V.as<T>(), *Z = ws.Z.as<T>(), *yv = ws.yv.as<T>(), *tv = ws.wv.as<T>();
   double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>(), *hp = ws.hpinned;
   double *h1 = hd, *h2 = hd + (kMaxRestart + 8), *nr = hd + 2 * (kMaxRestart + 8);
   double *cz = hd + 3 * (kMaxRestart + 8);
@@ -221,26 +224,25 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   int total = 0;
   while (true) {
     // V_0 = r / beta
-    vec_axpby(1.0 / beta, r, 0.0, V, n, st);
+    vec_convert<double, T>(r, V, n, 1.0 / beta, st);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j_end = 0;
     bool done = false;
     for (int j = 0; j < mr; ++j) {
-      double *vj = V + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
-      T *zj = Z + (int64_t)j * n;
-      block_apply<T>(Binv, vj, zj, m->n_nodes, nf, st);
-      if (coarse) coarse_apply_add<T>(m, vj, zj, st);
+      T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
+      T *zj = Z + (int64_t)j * ld;
+      precond_apply<T>(m, Binv, coarse, vj, zj, st);
       cudaEvent_t e0 = nullptr;
       TRY(tj.begin(st, &e0));
-      TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, yv, st));
+      TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, w, st));
       TRY(tj.end(st, e0));
-      vec_convert<T, double>(yv, w, n, 1.0, st);
       // classical Gram-Schmidt, a second pass only when the DGKS test asks;
       // V_{j+1} normalised on the device
       int *flag = reinterpret_cast<int *>(nr + 2);
-      vec_orthogonalize(V, n, j + 1, n, part, h1, h2, nr, flag, st);
-      vec_normalize(w, n, nr, flag, st);
+      T *scale = reinterpret_cast<T *>(nr + 3);
+      vec_orthogonalize<T>(V, ld, j + 1, n, part, h1, h2, nr, flag, scale, st);
+      vec_normalize<T>(w, n, scale, st);
       CHNS_CUDA_TRY(cudaMemcpyAsync(hp, hd, sizeof(double) * 3 * (kMaxRestart + 8), cudaMemcpyDeviceToHost, st));
       CHNS_CUDA_TRY(cudaStreamSynchronize(st));
       TRY(tj.collect());
@@ -277,7 +279,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
       yk[i] = s / H[i * mr + i];
     }
     CHNS_CUDA_TRY(cudaMemcpyAsync(cz, yk.data(), sizeof(double) * j_end, cudaMemcpyHostToDevice, st));
-    vec_combine<T>(Z, n, j_end, cz, x, n, st);
+    vec_combine<T>(Z, ld, j_end, cz, x, n, st);
     if (done || total >= o.krylov_max_it) break;
     // restart: r = b - J x
     vec_convert<double, T>(x, tv, n, 1.0, st);
@@ -285,8 +287,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     TRY(tj.begin(st, &e0));
     TRY(jacvec_prepared<T>(m, pc, ut, dl, tv, yv, st));
     TRY(tj.end(st, e0));
-    vec_convert<T, double>(yv, r, n, 1.0, st);
-    vec_lincomb(1.0, b, -1.0, r, r, n, st);
+    vec_sub<T>(b, yv, r, n, st);
     TRY(norm2(m, r, &beta, st));
     TRY(tj.collect());
     if (!std::isfinite(beta)) { set_error("non-finite Krylov residual"); return CHNS_ERR_NONFINITE; }

@@ -75,11 +75,20 @@ struct Coarse {
   int64_t ncn_inst = 0, nc0 = 0;    // coarse nodes / unknowns of one instance
   int64_t ncn = 0, nc = 0;          // coarse nodes, coarse unknowns (all instances)
   float *pos = nullptr;             // n_nodes * dim: node positions in coarse units
-  int64_t *rstart = nullptr;        // ncn + 1: restriction lists per coarse node
+  int64_t *rstart = nullptr;        // ncn + 1: restriction lists per coarse node (operator build)
   int32_t *rnode = nullptr;
   float *rw = nullptr;
+  // restriction in the Krylov loop: mesh nodes grouped by coarse cell and cut
+  // into pieces of at most kPiece nodes
+  int64_t ncell_inst = 0, ncell = 0, n_pieces = 0;
+  int32_t *cnodes = nullptr;        // n_nodes: node ids, cell by cell
+  int32_t *piece_cell = nullptr;    // n_pieces
+  int32_t *piece_begin = nullptr;   // n_pieces + 1: ranges in cnodes
+  int32_t *cell_piece = nullptr;    // ncell + 1: pieces of each cell
   DevBuf M;                         // per instance [A_c | I] -> [I | A_c^{-1}], nc0 x 2nc0 doubles
-  DevBuf vec;                       // coarse work vectors
+  DevBuf Minv32;                    // per instance A_c^{-1} rounded to float, nc0 x nc0
+  DevBuf vec;                       // coarse work vectors and operator-build partials
+  DevBuf rpart;                     // restriction partials, n_pieces x 2^dim x nf doubles
   bool ready = false;
   ~Coarse();
   void release();

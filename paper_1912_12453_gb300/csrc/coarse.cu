@@ -44,7 +44,20 @@ struct CGeo {
   int64_t n_nodes;
   int64_t ncn_inst;   // coarse nodes per instance
   int64_t nc0;        // coarse unknowns per instance
+  int64_t ncell_inst; // coarse cells per instance, (nc1 - 1)^dim
 };
+
+// 16 bytes of T
+template <typename T>
+struct alignas(16) V16 {
+  T a[16 / sizeof(T)];
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  return v;
+}
 
 // cell (lowest corner, per axis) and fraction of a position in coarse units
 __device__ __forceinline__ void locate(const CGeo &g, const float *pos, int *b, float *t) {
@@ -188,95 +201,184 @@ __global__ void k_gather_sum(CGeo g, int k, int f, const double *__restrict__ pa
   Ai[(lcp * nf + q) * ldA + int64_t(lin(g, oc)) * nf + f] = v;
 }
 
-// rc[c', q] = sum_i P[i, c'] v[i, q]: block (c', s) sums the s-th of kChunks
-// slices of c's restriction list; k_restrict_sum adds the slices in order
+constexpr int kPiece = 512;
 
-template <int NF>
-__global__ void __launch_bounds__(kB) k_restrict(const int64_t *__restrict__ rstart, const int32_t *__restrict__ rnode,
-                                                 const float *__restrict__ rw, const double *__restrict__ v,
-                                                 double *__restrict__ part) {
-  const int cp = blockIdx.x, sl = blockIdx.y;
-  const int64_t b0 = rstart[cp], len = rstart[cp + 1] - b0;
-  const int64_t lo = b0 + len * sl / kChunks, hi = b0 + len * (sl + 1) / kChunks;
-  double acc[NF];
+// rc = R v = P^T v, node by node.  The mesh nodes of each coarse cell are
+// stored together (cnodes) and cut into pieces; block p sums, for each of
+// its cell's 2^d corners, w_corner(i) v[i, q] over the piece, in T within
+// the block (fixed order; no FP64 instruction on the FP32 path, where the
+// FP64 pipe is the narrow one).  The weights are those of k_block_prolong,
+// so R is exactly P^T.
+template <typename T, int NF, int DIM>
+__global__ void __launch_bounds__(kB) k_restrict_cells(CGeo g, const float *__restrict__ pos,
+                                                       const int32_t *__restrict__ cnodes,
+                                                       const int32_t *__restrict__ piece_cell,
+                                                       const int32_t *__restrict__ piece_begin,
+                                                       const T *__restrict__ v, T *__restrict__ part) {
+  constexpr int NC = 1 << DIM;
+  const int p = blockIdx.x;
+  float base[3] = {0.f, 0.f, 0.f};
+  {
+    int r = int(piece_cell[p] % g.ncell_inst);
 #pragma unroll
-  for (int q = 0; q < NF; ++q) acc[q] = 0.0;
-  for (int64_t e = lo + threadIdx.x; e < hi; e += kB) {
-    const int64_t i = rnode[e];
-    const double wgt = rw[e];
-#pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] += wgt * v[i * NF + q];
+    for (int a = 0; a < DIM; ++a) { base[a] = float(r % (g.nc1 - 1)); r /= (g.nc1 - 1); }
   }
-  __shared__ double red[kB / 32][NF];
+  T acc[NC][NF];
 #pragma unroll
-  for (int q = 0; q < NF; ++q) {
-    double s = warp_sum(acc[q]);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = s;
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[c][q] = T(0);
+  const int e1 = piece_begin[p + 1];
+  for (int e = piece_begin[p] + threadIdx.x; e < e1; e += kB) {
+    const int64_t i = cnodes[e];
+    T t[DIM], x[NF];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) t[a] = T(pos[i * DIM + a] - base[a]);
+#pragma unroll
+    for (int q = 0; q < NF; ++q) x[q] = v[i * NF + q];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T wc = T(1);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) wc *= ((c >> a) & 1) ? t[a] : T(1) - t[a];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) acc[c][q] = fma(wc, x[q], acc[c][q]);
+    }
   }
+  __shared__ T red[kB / 32][NC * NF];
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+      const T sum = warp_sum_t(acc[c][q]);
+      if (ln == 0) red[wid][c * NF + q] = sum;
+    }
   __syncthreads();
-  if (threadIdx.x < NF) {
-    double s = 0.0;
-    for (int w = 0; w < kB / 32; ++w) s += red[w][threadIdx.x];
-    part[(int64_t(cp) * kChunks + sl) * NF + threadIdx.x] = s;
+  for (int k = threadIdx.x; k < NC * NF; k += kB) {
+    T sum = T(0);
+#pragma unroll
+    for (int w = 0; w < kB / 32; ++w) sum += red[w][k];
+    part[int64_t(p) * NC * NF + k] = sum;
   }
 }
 
-__global__ void k_restrict_sum(const double *__restrict__ part, int64_t nc, int nf, double *__restrict__ rc) {
-  const int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x;
-  if (t >= nc) return;
-  const int64_t c = t / nf, q = t % nf;
-  double s = 0.0;
-  for (int sl = 0; sl < kChunks; ++sl) s += part[(c * kChunks + sl) * nf + q];
-  rc[t] = s;
+// rc[c', q]: the corner sums of the cells around coarse node c' (each cell's
+// pieces in order), one warp per coarse unknown, double sums
+template <typename T, int DIM>
+__global__ void k_restrict_sum(CGeo g, int64_t ncn, const int32_t *__restrict__ cell_piece,
+                               const T *__restrict__ part, T *__restrict__ rc) {
+  constexpr int NC = 1 << DIM;
+  const int64_t t = (blockIdx.x * int64_t(kB) + threadIdx.x) >> 5;
+  const int ln = threadIdx.x & 31;
+  const int nf = g.nf;
+  if (t >= ncn * nf) return;
+  const int64_t cp = t / nf, inst = cp / g.ncn_inst;
+  const int q = int(t % nf);
+  int cc[3] = {0, 0, 0};
+  {
+    int r = int(cp % g.ncn_inst);
+    for (int a = 0; a < DIM; ++a) { cc[a] = r % g.nc1; r /= g.nc1; }
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    int cell = 0;
+    bool ok = true;
+    for (int a = DIM - 1; a >= 0; --a) {
+      const int ca = cc[a] - ((s >> a) & 1);
+      if (ca < 0 || ca > g.nc1 - 2) ok = false;
+      cell = cell * (g.nc1 - 1) + ca;
+    }
+    if (!ok) continue;
+    const int64_t gc = inst * g.ncell_inst + cell;
+    for (int p = cell_piece[gc] + ln; p < cell_piece[gc + 1]; p += 32)
+      sum += double(part[(int64_t(p) * NC + s) * nf + q]);
+  }
+  sum = warp_sum(sum);
+  if (ln == 0) rc[t] = T(sum);
 }
 
-// zc = Ainv rc, one warp per row; Ainv is the right half of [A | I] after
-// Gauss-Jordan (row stride 2 nc)
-__global__ void k_coarse_matvec(const double *__restrict__ M, int64_t nc, int64_t nc0,
-                                const double *__restrict__ rc, double *__restrict__ zc) {
+// zc = A_c^{-1} rc, one warp per row, in precision T; row r of instance i at
+// Minv + i * inst_stride + (r % nc0) * ld
+template <typename T>
+__global__ void k_coarse_matvec(const T *__restrict__ Minv, int64_t ld, int64_t inst_stride, int64_t nc,
+                                int64_t nc0, const T *__restrict__ rc, T *__restrict__ zc) {
   const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int ln = threadIdx.x & 31;
   if (r >= nc) return;
   const int64_t inst = r / nc0, lr = r % nc0;
-  const double *row = M + inst * nc0 * 2 * nc0 + lr * 2 * nc0 + nc0;
-  const double *x = rc + inst * nc0;
-  double s = 0.0;
-  for (int64_t c = ln; c < nc0; c += 32) s += row[c] * x[c];
-  s = warp_sum(s);
+  const T *row = Minv + inst * inst_stride + lr * ld;
+  const T *x = rc + inst * nc0;
+  T s = T(0);
+  for (int64_t c = ln; c < nc0; c += 32) s = fma(row[c], x[c], s);
+  s = warp_sum_t(s);
   if (ln == 0) zc[r] = s;
 }
 
-// z[i, q] += sum_c P[i, c] zc[c, q]
+// z = Binv v + P zc  (nodal block-Jacobi plus the prolonged coarse
+// correction; zc == nullptr: block-Jacobi only)
 template <typename T, int NF, int DIM>
-__global__ void __launch_bounds__(kB) k_prolong_add(CGeo g, const float *__restrict__ pos,
-                                                    const int32_t *__restrict__ node_inst,
-                                                    const double *__restrict__ zc, T *__restrict__ z) {
+__global__ void __launch_bounds__(kB) k_block_prolong(CGeo g, const float *__restrict__ pos,
+                                                      const int32_t *__restrict__ node_inst,
+                                                      const T *__restrict__ Binv, const T *__restrict__ v,
+                                                      const T *__restrict__ zc, T *__restrict__ z) {
   for (int64_t i = blockIdx.x * int64_t(kB) + threadIdx.x; i < g.n_nodes; i += int64_t(gridDim.x) * kB) {
-    int b[3];
-    float t[3];
-    locate(g, pos + i * g.dim, b, t);
-    const int64_t cbase = node_inst ? int64_t(node_inst[i]) * g.ncn_inst : 0;
-    double acc[NF];
+    T x[NF], acc[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NF; ++q) { x[q] = v[i * NF + q]; acc[q] = T(0); }
+    if (zc) {
+      int b[3];
+      float tf[3];
+      locate(g, pos + i * DIM, b, tf);
+      const int64_t cbase = node_inst ? int64_t(node_inst[i]) * g.ncn_inst : 0;
+      T t[DIM];
 #pragma unroll
-    for (int c = 0; c < (1 << DIM); ++c) {
-      int cc[3] = {0, 0, 0};
-      double wc = 1.0;
+      for (int a = 0; a < DIM; ++a) t[a] = T(tf[a]);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        cc[a] = b[a] + ((c >> a) & 1);
-        wc *= ((c >> a) & 1) ? double(t[a]) : 1.0 - double(t[a]);
+      for (int c = 0; c < (1 << DIM); ++c) {
+        T wc = T(1);
+        int64_t idx = 0;
+#pragma unroll
+        for (int a = DIM - 1; a >= 0; --a) idx = idx * g.nc1 + b[a] + ((c >> a) & 1);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wc *= ((c >> a) & 1) ? t[a] : T(1) - t[a];
+        const T *zp = zc + (cbase + idx) * NF;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) acc[q] = fma(wc, zp[q], acc[q]);
       }
-      int64_t idx = 0;
+    }
+    T B[NF * NF];
+    if constexpr ((NF * NF * sizeof(T)) % 16 == 0) {
+      constexpr int L = 16 / sizeof(T);
+      const V16<T> *Bv = reinterpret_cast<const V16<T> *>(Binv + i * NF * NF);
 #pragma unroll
-      for (int a = DIM - 1; a >= 0; --a) idx = idx * g.nc1 + cc[a];
-      const double *zp = zc + (cbase + idx) * NF;
+      for (int k = 0; k < NF * NF / L; ++k) {
+        const V16<T> b = Bv[k];
 #pragma unroll
-      for (int q = 0; q < NF; ++q) acc[q] += wc * zp[q];
+        for (int l = 0; l < L; ++l) B[k * L + l] = b.a[l];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NF * NF; ++k) B[k] = Binv[i * NF * NF + k];
     }
 #pragma unroll
-    for (int q = 0; q < NF; ++q) z[i * NF + q] += T(acc[q]);
+    for (int r = 0; r < NF; ++r) {
+      T s = acc[r];
+#pragma unroll
+      for (int c = 0; c < NF; ++c) s = fma(B[r * NF + c], x[c], s);
+      z[i * NF + r] = s;
+    }
+  }
+}
+
+// A_c^{-1} of every instance rounded to T, compact (nc0 x nc0 each)
+template <typename T>
+__global__ void k_extract_inverse(const double *__restrict__ M, int64_t nc0, int n_inst, T *__restrict__ out) {
+  const int64_t per = nc0 * nc0;
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < per * n_inst; t += int64_t(gridDim.x) * kB) {
+    const int64_t inst = t / per, r = (t % per) / nc0, c = t % nc0;
+    out[t] = T(M[inst * nc0 * 2 * nc0 + r * 2 * nc0 + nc0 + c]);
   }
 }
 
@@ -354,12 +456,20 @@ void Coarse::release() {
   cudaFree(rstart);
   cudaFree(rnode);
   cudaFree(rw);
+  cudaFree(cnodes);
+  cudaFree(piece_cell);
+  cudaFree(piece_begin);
+  cudaFree(cell_piece);
   pos = nullptr;
   rstart = nullptr;
   rnode = nullptr;
   rw = nullptr;
+  cnodes = piece_cell = piece_begin = cell_piece = nullptr;
+  ncell_inst = ncell = n_pieces = 0;
   M.release();
+  Minv32.release();
   vec.release();
+  rpart.release();
   level = -1;
   ready = false;
 }
@@ -424,6 +534,46 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   CHNS_CUDA_TRY(cudaMemcpy(C.rnode, rnode.data(), sizeof(int32_t) * rnode.size(), cudaMemcpyHostToDevice));
   CHNS_CUDA_TRY(cudaMalloc(&C.rw, sizeof(float) * std::max<size_t>(rw.size(), 1)));
   CHNS_CUDA_TRY(cudaMemcpy(C.rw, rw.data(), sizeof(float) * rw.size(), cudaMemcpyHostToDevice));
+  // nodes grouped by coarse cell (stable: node order within a cell), pieces
+  int64_t ncell_inst = 1;
+  for (int a = 0; a < dim; ++a) ncell_inst *= (nc1 - 1);
+  const int64_t ncell = ncell_inst * ni;
+  std::vector<int64_t> ccnt(ncell + 1, 0);
+  std::vector<int64_t> cell_of(m->n_nodes);
+  for (int64_t i = 0; i < m->n_nodes; ++i) {
+    int64_t c = 0;
+    for (int a = dim - 1; a >= 0; --a) c = c * (nc1 - 1) + base[i * dim + a];
+    cell_of[i] = cbase[i] / ncn * ncell_inst + c;
+    ccnt[cell_of[i] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) ccnt[c + 1] += ccnt[c];
+  std::vector<int32_t> cnodes(m->n_nodes);
+  {
+    std::vector<int64_t> f(ccnt.begin(), ccnt.end() - 1);
+    for (int64_t i = 0; i < m->n_nodes; ++i) cnodes[f[cell_of[i]]++] = (int32_t)i;
+  }
+  std::vector<int32_t> piece_cell, piece_begin, cell_piece(ncell + 1, 0);
+  for (int64_t c = 0; c < ncell; ++c) {
+    cell_piece[c] = (int32_t)piece_cell.size();
+    for (int64_t b = ccnt[c]; b < ccnt[c + 1]; b += kPiece) {
+      piece_cell.push_back((int32_t)c);
+      piece_begin.push_back((int32_t)b);
+    }
+  }
+  cell_piece[ncell] = (int32_t)piece_cell.size();
+  piece_begin.push_back((int32_t)m->n_nodes);
+  const int64_t np = (int64_t)piece_cell.size();
+  CHNS_CUDA_TRY(cudaMalloc(&C.cnodes, sizeof(int32_t) * std::max<size_t>(cnodes.size(), 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.cnodes, cnodes.data(), sizeof(int32_t) * cnodes.size(), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.piece_cell, sizeof(int32_t) * std::max<int64_t>(np, 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.piece_cell, piece_cell.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.piece_begin, sizeof(int32_t) * (np + 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.piece_begin, piece_begin.data(), sizeof(int32_t) * (np + 1), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.cell_piece, sizeof(int32_t) * (ncell + 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.cell_piece, cell_piece.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice));
+  C.ncell_inst = ncell_inst;
+  C.ncell = ncell;
+  C.n_pieces = np;
   C.level = Lc;
   C.nc1 = nc1;
   C.n_inst = ni;
@@ -432,7 +582,9 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   C.ncn = ncn_all;
   C.nc = ncn_all * nf;
   TRY_CHNS(C.M.ensure(sizeof(double) * C.nc0 * 2 * C.nc0 * ni));
-  TRY_CHNS(C.vec.ensure(sizeof(double) * (3 * C.nc + 8 + C.nc * kChunks + C.ncn * kChunks * 8 * nf)));
+  TRY_CHNS(C.Minv32.ensure(sizeof(float) * C.nc0 * C.nc0 * ni));
+  TRY_CHNS(C.vec.ensure(sizeof(double) * (3 * C.nc + 8 + C.ncn * kChunks * 8 * nf)));
+  TRY_CHNS(C.rpart.ensure(sizeof(double) * std::max<int64_t>(np, 1) * (1 << dim) * nf));
   return CHNS_OK;
 }
 
@@ -440,12 +592,12 @@ template <typename T>
 chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaStream_t st) {
   Coarse &C = m->coarse;
   const int nf = m->nf, dim = m->dim;
-  CGeo g{dim, nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0};
+  CGeo g{dim, nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0, C.ncell_inst};
   double *M = C.M.as<double>();
   const int64_t nc0 = C.nc0;
   CHNS_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nc0 * 2 * nc0 * C.n_inst, st));
   const int ncol = dim == 2 ? 9 : 27;
-  double *part = C.vec.as<double>() + 3 * C.nc + 8 + C.nc * kChunks;
+  double *part = C.vec.as<double>() + 3 * C.nc + 8;
   for (int k = 0; k < ncol; ++k)
     for (int f = 0; f < nf; ++f) {
       if (dim == 2) k_probe_coarse<T, 5, 2><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, k, f, w);
@@ -476,6 +628,8 @@ chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaSt
   CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   CHNS_CUDA_TRY(cudaStreamSynchronize(st));
   if (hbad) { set_error("singular coarse operator"); return CHNS_ERR_KRYLOV; }
+  k_extract_inverse<float><<<grid_n(nc0 * nc0 * C.n_inst), kB, 0, st>>>(M, nc0, C.n_inst, C.Minv32.as<float>());
+  note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error("coarse build: %s", cudaGetErrorString(e)); return CHNS_ERR_CUDA; }
   C.ready = true;
@@ -484,22 +638,41 @@ chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaSt
 template chns_status coarse_build<float>(chns_mesh *, JvFn<float>, void *, float *, float *, cudaStream_t);
 template chns_status coarse_build<double>(chns_mesh *, JvFn<double>, void *, double *, double *, cudaStream_t);
 
+// z = B^{-1} v (+ P A_c^{-1} R v when the coarse space is ready and wanted)
 template <typename T>
-void coarse_apply_add(chns_mesh *m, const double *v, T *z, cudaStream_t st) {
+void precond_apply(chns_mesh *m, const T *Binv, bool coarse, const T *v, T *z, cudaStream_t st) {
   Coarse &C = m->coarse;
-  CGeo g{m->dim, m->nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0};
-  double *rc = C.vec.as<double>(), *zc = rc + C.nc, *part = rc + 3 * C.nc + 8;
-  dim3 gr((unsigned)C.ncn, kChunks);
-  if (m->nf == 5) k_restrict<5><<<gr, kB, 0, st>>>(C.rstart, C.rnode, C.rw, v, part);
-  else k_restrict<6><<<gr, kB, 0, st>>>(C.rstart, C.rnode, C.rw, v, part);
-  k_restrict_sum<<<(unsigned)((C.nc + kB - 1) / kB), kB, 0, st>>>(part, C.nc, m->nf, rc);
-  k_coarse_matvec<<<(unsigned)((C.nc * 32 + kB - 1) / kB), kB, 0, st>>>(C.M.as<double>(), C.nc, C.nc0, rc, zc);
-  const int32_t *ni = m->n_inst > 1 ? m->node_inst : nullptr;
-  if (m->dim == 2) k_prolong_add<T, 5, 2><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, zc, z);
-  else k_prolong_add<T, 6, 3><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, zc, z);
-  note_launches(4);
+  const bool use = coarse && C.ready;
+  CGeo g{m->dim, m->nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0, C.ncell_inst};
+  T *rc = nullptr, *zc = nullptr;
+  if (use) {
+    rc = reinterpret_cast<T *>(C.vec.as<double>());
+    zc = reinterpret_cast<T *>(C.vec.as<double>() + C.nc);
+    T *part = reinterpret_cast<T *>(C.rpart.as<double>());
+    const unsigned np = (unsigned)C.n_pieces;
+    const unsigned gs = (unsigned)((C.nc * 32 + kB - 1) / kB);
+    if (m->dim == 2) {
+      k_restrict_cells<T, 5, 2><<<np, kB, 0, st>>>(g, C.pos, C.cnodes, C.piece_cell, C.piece_begin, v, part);
+      k_restrict_sum<T, 2><<<gs, kB, 0, st>>>(g, C.ncn, C.cell_piece, part, rc);
+    } else {
+      k_restrict_cells<T, 6, 3><<<np, kB, 0, st>>>(g, C.pos, C.cnodes, C.piece_cell, C.piece_begin, v, part);
+      k_restrict_sum<T, 3><<<gs, kB, 0, st>>>(g, C.ncn, C.cell_piece, part, rc);
+    }
+    const unsigned gm = (unsigned)((C.nc * 32 + kB - 1) / kB);
+    if (sizeof(T) == sizeof(float))
+      k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.Minv32.as<float>()), C.nc0,
+                                            C.nc0 * C.nc0, C.nc, C.nc0, rc, zc);
+    else
+      k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.M.as<double>() + C.nc0), 2 * C.nc0,
+                                            2 * C.nc0 * C.nc0, C.nc, C.nc0, rc, zc);
+    note_launches(3);
+  }
+  const int32_t *ni = (use && m->n_inst > 1) ? m->node_inst : nullptr;
+  if (m->dim == 2) k_block_prolong<T, 5, 2><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, Binv, v, zc, z);
+  else k_block_prolong<T, 6, 3><<<grid_n(m->n_nodes), kB, 0, st>>>(g, C.pos, ni, Binv, v, zc, z);
+  note_launches(1);
 }
-template void coarse_apply_add<float>(chns_mesh *, const double *, float *, cudaStream_t);
-template void coarse_apply_add<double>(chns_mesh *, const double *, double *, cudaStream_t);
+template void precond_apply<float>(chns_mesh *, const float *, bool, const float *, float *, cudaStream_t);
+template void precond_apply<double>(chns_mesh *, const double *, bool, const double *, double *, cudaStream_t);
 
 }  // namespace chns

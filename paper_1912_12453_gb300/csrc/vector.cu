@@ -19,126 +19,63 @@ inline unsigned grid_n(int64_t n) {
   return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 8);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// FP64 instructions run on a narrow pipe on this part (tens of times slower
+// than FP32, per warp instruction, whatever the active lanes), so the FP32
+// Krylov kernels keep every per-element and per-block step in float: 16-byte
+// loads, float products and sums within a thread, a warp and a block (fixed
+// order), one float partial per block.  Only the final sum of the block
+// partials is in double.  With the FP64 path (T = double) the same kernels
+// run in double.
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
   return v;
 }
 
-// block sum of NV values per thread -> out[NV * blockIdx.x + k]
-template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out) {
-  __shared__ double sh[NV][kB / 32];
+// 16 bytes of T: 4 floats or 2 doubles
+template <typename T>
+struct alignas(16) V16 {
+  static constexpr int L = 16 / sizeof(T);
+  T a[L];
+};
+
+// block sums of NV per-thread values (fixed order) -> out[k * gridDim.x + blockIdx.x]
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_store(T (&v)[NV], T *out) {
+  __shared__ T sh[NV][kB / 32];
   const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = warp_sum(v[k]);
+    const T s = warp_sum(v[k]);
     if (ln == 0) sh[k][wid] = s;
   }
   __syncthreads();
   if (threadIdx.x < NV) {
-    double s = 0.0;
+    T s = T(0);
+#pragma unroll
     for (int w = 0; w < kB / 32; ++w) s += sh[threadIdx.x][w];
     out[(int64_t)gridDim.x * threadIdx.x + blockIdx.x] = s;
   }
 }
 
-// partial[k * nblocks + b] for k < nv -> res[k]; fixed order
-__global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, int nv,
-                               double *__restrict__ res) {
+// res[k] = sum_b partial[k * nblocks + b] (double, fixed order), k < nv.
+// Skipped (res[k] = 0) when flag is given and *flag == 0.  Optional outputs
+// for a squared norm (nv == 1): scale = 1/sqrt(res) in P (0 if res <= 0) and
+// the DGKS flag = (res < 1e-4 * before): the first projection removed more
+// than 99.99% of |w|^2, so a second Gram-Schmidt pass is needed.
+template <typename P>
+__global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int nv, double *__restrict__ res,
+                               const int *__restrict__ flag, P *__restrict__ scale,
+                               const double *__restrict__ before, int *__restrict__ flag_out) {
   const int k = blockIdx.x;
   if (k >= nv) return;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)k * nblocks + b];
-  __shared__ double sh[kB / 32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    res[k] = t;
-  }
-}
-
-// h[i] = V_i . w for i in [i0, i0 + NV)   (V_i at V + i * ld)
-template <int NV>
-__global__ void __launch_bounds__(kB) k_multidot(const double *__restrict__ V, int64_t ld, int i0, int nv,
-                                                 const double *__restrict__ w, int64_t n,
-                                                 double *__restrict__ partial) {
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
-    double x = w[t];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) acc[k] += V[(int64_t)(i0 + k) * ld + t] * x;
-  }
-  block_sum_store<NV>(acc, partial + (int64_t)i0 * gridDim.x);
-}
-
-// w -= sum_i h[i] V_i, i < nv
-__global__ void __launch_bounds__(kB) k_update(const double *__restrict__ V, int64_t ld, int nv,
-                                               const double *__restrict__ h, double *__restrict__ w,
-                                               int64_t n) {
-  __shared__ double hs[kMaxRestart + 1];
-  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = h[i];
-  __syncthreads();
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
-    double s = w[t];
-    for (int i = 0; i < nv; ++i) s -= hs[i] * V[(int64_t)i * ld + t];
-    w[t] = s;
-  }
-}
-
-// w -= sum_i h[i] V_i (i < nv) and per-block partial sums of the new |w|^2;
-// skipped entirely when flag is given and *flag == 0
-__global__ void __launch_bounds__(kB) k_update_norm(const double *__restrict__ V, int64_t ld, int nv,
-                                                    const double *__restrict__ h, double *__restrict__ w,
-                                                    int64_t n, const int *__restrict__ flag,
-                                                    double *__restrict__ partial) {
-  if (flag && *flag == 0) return;
-  __shared__ double hs[kMaxRestart + 1];
-  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = h[i];
-  __syncthreads();
-  double acc[1] = {0.0};
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
-    double s = w[t];
-    for (int i = 0; i < nv; ++i) s -= hs[i] * V[(int64_t)i * ld + t];
-    w[t] = s;
-    acc[0] += s * s;
-  }
-  block_sum_store<1>(acc, partial);
-}
-
-// multi-dot that is skipped when *flag == 0
-template <int NV>
-__global__ void __launch_bounds__(kB) k_multidot_if(const double *__restrict__ V, int64_t ld, int i0, int nv,
-                                                    const double *__restrict__ w, int64_t n,
-                                                    double *__restrict__ partial, const int *__restrict__ flag) {
-  if (*flag == 0) return;
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
-    double x = w[t];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) acc[k] += V[(int64_t)(i0 + k) * ld + t] * x;
-  }
-  block_sum_store<NV>(acc, partial + (int64_t)i0 * gridDim.x);
-}
-
-__global__ void k_sum_partials_if(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ res,
-                                  const int *__restrict__ flag) {
-  const int k = blockIdx.x;
-  if (k >= nv) return;
-  if (*flag == 0) {
+  if (flag && *flag == 0) {
     if (threadIdx.x == 0) res[k] = 0.0;
     return;
   }
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)k * nblocks + b];
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += double(partial[(int64_t)k * nblocks + b]);
   __shared__ double sh[kB / 32];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -147,31 +84,105 @@ __global__ void k_sum_partials_if(const double *__restrict__ partial, int nblock
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
     res[k] = t;
+    if (scale) *scale = t > 0.0 ? P(1.0 / sqrt(t)) : P(0);
+    if (flag_out) *flag_out = (t < 1e-4 * before[0]) ? 1 : 0;
   }
 }
 
-// Reorthogonalise only on severe cancellation: the first projection removed
-// more than 99.99% of |w|^2 (|w| dropped below 1% of its length); the
-// Newton corrections need a linear reduction of ~1e-3 only
-__global__ void k_reorth_flag(const double *__restrict__ before, const double *__restrict__ after,
-                              int *__restrict__ flag) {
-  *flag = (after[0] < 1e-4 * before[0]) ? 1 : 0;
+// partial sums of V_{i0+k} . w, k < nv <= NV; V_i at V + i * ld with ld a
+// multiple of 16 bytes / sizeof(T) and V 16-byte aligned; skipped when flag
+// is given and *flag == 0
+template <typename T, int NV>
+__global__ void __launch_bounds__(kB) k_multidot(const T *__restrict__ V, int64_t ld, int i0, int nv,
+                                                 const T *__restrict__ w, int64_t n, T *__restrict__ partial,
+                                                 const int *__restrict__ flag) {
+  if (flag && *flag == 0) return;
+  constexpr int L = V16<T>::L;
+  T acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = T(0);
+  const int64_t nl = n / L;
+  const V16<T> *wv = reinterpret_cast<const V16<T> *>(w);
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nl; t += int64_t(gridDim.x) * kB) {
+    const V16<T> x = wv[t];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nv) {
+        const V16<T> a = reinterpret_cast<const V16<T> *>(V + (int64_t)(i0 + k) * ld)[t];
+#pragma unroll
+        for (int l = 0; l < L; ++l) acc[k] = fma(a.a[l], x.a[l], acc[k]);
+      }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < n - nl * L) {
+    const int64_t t = nl * L + threadIdx.x;
+    const T x = w[t];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nv) acc[k] = fma(V[(int64_t)(i0 + k) * ld + t], x, acc[k]);
+  }
+  block_sum_store<T, NV>(acc, partial + (int64_t)i0 * gridDim.x);
 }
 
-// out = x / sqrt(chosen |w|^2): n2[0] if *flag else n1[0]
-__global__ void k_normalize(double *__restrict__ w, int64_t n, const double *__restrict__ n1,
-                            const double *__restrict__ n2, const int *__restrict__ flag) {
-  const double q = *flag ? n2[0] : n1[0];
-  if (!(q > 0.0)) return;
-  const double s = 1.0 / sqrt(q);
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) w[t] *= s;
+// w -= sum_i h[i] V_i (i < nv) and block partial sums of the new |w|^2;
+// skipped when flag is given and *flag == 0.  Layout as k_multidot.
+template <typename T>
+__global__ void __launch_bounds__(kB) k_update_norm(const T *__restrict__ V, int64_t ld, int nv,
+                                                    const double *__restrict__ h, T *__restrict__ w, int64_t n,
+                                                    const int *__restrict__ flag, T *__restrict__ partial) {
+  if (flag && *flag == 0) return;
+  constexpr int L = V16<T>::L;
+  __shared__ T hs[kMaxRestart + 1];
+  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = T(-h[i]);
+  __syncthreads();
+  T acc[1] = {T(0)};
+  const int64_t nl = n / L;
+  V16<T> *wv = reinterpret_cast<V16<T> *>(w);
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nl; t += int64_t(gridDim.x) * kB) {
+    V16<T> s = wv[t];
+#pragma unroll 4
+    for (int i = 0; i < nv; ++i) {
+      const V16<T> a = reinterpret_cast<const V16<T> *>(V + (int64_t)i * ld)[t];
+#pragma unroll
+      for (int l = 0; l < L; ++l) s.a[l] = fma(hs[i], a.a[l], s.a[l]);
+    }
+    wv[t] = s;
+#pragma unroll
+    for (int l = 0; l < L; ++l) acc[0] = fma(s.a[l], s.a[l], acc[0]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < n - nl * L) {
+    const int64_t t = nl * L + threadIdx.x;
+    T s = w[t];
+    for (int i = 0; i < nv; ++i) s = fma(hs[i], V[(int64_t)i * ld + t], s);
+    w[t] = s;
+    acc[0] = fma(s, s, acc[0]);
+  }
+  block_sum_store<T, 1>(acc, partial);
 }
 
-// out = x / nrm[0]
-__global__ void k_scale_by(const double *__restrict__ x, const double *__restrict__ nrm, double *__restrict__ out,
-                           int64_t n) {
-  double s = 1.0 / nrm[0];
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) out[t] = x[t] * s;
+// partial sums of x . y (double, any alignment)
+__global__ void __launch_bounds__(kB) k_dot(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                            double *__restrict__ partial) {
+  double acc[1] = {0.0};
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB)
+    acc[0] = fma(x[t], y[t], acc[0]);
+  block_sum_store<double, 1>(acc, partial);
+}
+
+// w *= *scale (a zero scale: |w| = 0, w is left as is)
+template <typename T>
+__global__ void k_normalize(T *__restrict__ w, int64_t n, const T *__restrict__ scale) {
+  const T s = *scale;
+  if (s == T(0)) return;
+  constexpr int L = V16<T>::L;
+  const int64_t nl = n / L;
+  V16<T> *wv = reinterpret_cast<V16<T> *>(w);
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nl; t += int64_t(gridDim.x) * kB) {
+    V16<T> x = wv[t];
+#pragma unroll
+    for (int l = 0; l < L; ++l) x.a[l] *= s;
+    wv[t] = x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < n - nl * L) w[nl * L + threadIdx.x] *= s;
 }
 
 template <typename A, typename B>
@@ -180,18 +191,26 @@ __global__ void k_convert(const A *__restrict__ x, B *__restrict__ y, int64_t n,
     y[t] = B(a * double(x[t]));
 }
 
-// x += sum_j c[j] Z_j
+// x += sum_j c[j] Z_j: the combination in the precision T of Z (it is a
+// Krylov correction, accurate to the Krylov tolerance), added to x in double
 template <typename T>
 __global__ void k_combine(const T *__restrict__ Z, int64_t ld, int nz, const double *__restrict__ c,
                           double *__restrict__ x, int64_t n) {
-  __shared__ double cs[kMaxRestart];
-  for (int i = threadIdx.x; i < nz; i += kB) cs[i] = c[i];
+  __shared__ T cs[kMaxRestart];
+  for (int i = threadIdx.x; i < nz; i += kB) cs[i] = T(c[i]);
   __syncthreads();
   for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) {
-    double s = x[t];
-    for (int j = 0; j < nz; ++j) s += cs[j] * double(Z[(int64_t)j * ld + t]);
-    x[t] = s;
+    T s = T(0);
+    for (int j = 0; j < nz; ++j) s = fma(cs[j], Z[(int64_t)j * ld + t], s);
+    x[t] += double(s);
   }
+}
+
+// r = b - y  (y in the element precision)
+template <typename T>
+__global__ void k_sub(const double *__restrict__ b, const T *__restrict__ y, double *__restrict__ r, int64_t n) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB)
+    r[t] = b[t] - double(y[t]);
 }
 
 // y = a x + b y
@@ -263,14 +282,14 @@ __global__ void k_invert_blocks(T *__restrict__ B, int64_t n_nodes, int *__restr
     for (int c = 0; c < NF; ++c) B[(a * NF + r) * NF + c] = T(M[r][NF + c]);
 }
 
-// z = Binv v  (v double, z and Binv in T)
+// z = Binv v  (all in T)
 template <typename T, int NF>
-__global__ void __launch_bounds__(kB) k_block_apply(const T *__restrict__ Binv, const double *__restrict__ v,
+__global__ void __launch_bounds__(kB) k_block_apply(const T *__restrict__ Binv, const T *__restrict__ v,
                                                     T *__restrict__ z, int64_t n_nodes) {
   for (int64_t a = blockIdx.x * int64_t(kB) + threadIdx.x; a < n_nodes; a += int64_t(gridDim.x) * kB) {
     T x[NF];
 #pragma unroll
-    for (int c = 0; c < NF; ++c) x[c] = T(v[a * NF + c]);
+    for (int c = 0; c < NF; ++c) x[c] = v[a * NF + c];
     const T *b = Binv + a * NF * NF;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
@@ -287,62 +306,70 @@ __global__ void __launch_bounds__(kB) k_block_apply(const T *__restrict__ Binv, 
 // ---------------------------------------------------------------- launchers
 int red_blocks() { return kRedBlocks; }
 
-void vec_multidot(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial,
-                  double *h, cudaStream_t st) {
+template <typename T>
+void vec_multidot(const T *V, int64_t ld, int nv, const T *w, int64_t n, double *partial, double *h,
+                  cudaStream_t st, const int *flag) {
+  T *pt = reinterpret_cast<T *>(partial);
   for (int i0 = 0; i0 < nv; i0 += 8) {
     int c = std::min(8, nv - i0);
-    k_multidot<8><<<kRedBlocks, kB, 0, st>>>(V, ld, i0, c, w, n, partial);
+    k_multidot<T, 8><<<kRedBlocks, kB, 0, st>>>(V, ld, i0, c, w, n, pt, flag);
     note_launches(1);
   }
-  k_sum_partials<<<nv, kB, 0, st>>>(partial, kRedBlocks, nv, h);
+  k_sum_partials<T><<<nv, kB, 0, st>>>(pt, kRedBlocks, nv, h, flag, nullptr, nullptr, nullptr);
   note_launches(1);
 }
+template void vec_multidot<float>(const float *, int64_t, int, const float *, int64_t, double *, double *,
+                                  cudaStream_t, const int *);
+template void vec_multidot<double>(const double *, int64_t, int, const double *, int64_t, double *, double *,
+                                   cudaStream_t, const int *);
 
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st) {
-  k_multidot<1><<<kRedBlocks, kB, 0, st>>>(x, 0, 0, 1, y, n, partial);
-  note_launches(1);
-  k_sum_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, res);
-  note_launches(1);
+  k_dot<<<kRedBlocks, kB, 0, st>>>(x, y, n, partial);
+  k_sum_partials<double><<<1, kB, 0, st>>>(partial, kRedBlocks, 1, res, nullptr, nullptr, nullptr, nullptr);
+  note_launches(2);
 }
 
 // One Arnoldi orthogonalisation of w = V_{nv} against V_0..V_{nv-1} (classical
-// Gram-Schmidt, a second pass only on severe cancellation), then
-// normalisation of w when its norm is nonzero.  Device outputs (no host sync):
-// h1[0..nv-1] first-pass coefficients, h1[nv] = |w|^2 before; h2[0..nv-1]
-// second-pass coefficients (0 if skipped); nrm[0] = |w|^2 after pass 1,
-// nrm[1] = after pass 2, flag[0] = whether pass 2 ran.
-void vec_orthogonalize(double *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
-                       double *nrm, int *flag, cudaStream_t st) {
+// Gram-Schmidt, a second pass only on severe cancellation).  Device outputs
+// (no host sync): h1[0..nv-1] first-pass coefficients, h1[nv] = |w|^2
+// before; h2[0..nv-1] second-pass coefficients (0 if skipped); nrm[0] =
+// |w|^2 after pass 1, nrm[1] = after pass 2, flag[0] = whether pass 2 ran,
+// *scale = 1/|w| for vec_normalize.
+template <typename T>
+void vec_orthogonalize(T *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
+                       double *nrm, int *flag, T *scale, cudaStream_t st) {
+  T *pt = reinterpret_cast<T *>(partial);
   // pass 1 dots include w itself (stored right after V_{nv-1}): |w|^2
-  vec_multidot(V, ld, nv + 1, V + (int64_t)nv * ld, n, partial, h1, st);
-  double *w = V + (int64_t)nv * ld;
-  k_update_norm<<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h1, w, n, nullptr, partial);
-  k_sum_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, nrm);
-  k_reorth_flag<<<1, 1, 0, st>>>(h1 + nv, nrm, flag);
-  for (int i0 = 0; i0 < nv; i0 += 8) {
-    int c = std::min(8, nv - i0);
-    k_multidot_if<8><<<kRedBlocks, kB, 0, st>>>(V, ld, i0, c, w, n, partial, flag);
-  }
-  k_sum_partials_if<<<nv, kB, 0, st>>>(partial, kRedBlocks, nv, h2, flag);
-  k_update_norm<<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h2, w, n, flag, partial);
-  k_sum_partials_if<<<1, kB, 0, st>>>(partial, kRedBlocks, 1, nrm + 1, flag);
-  note_launches(6 + (nv + 7) / 8 + (nv + 1 + 7) / 8 + 1);
+  vec_multidot<T>(V, ld, nv + 1, V + (int64_t)nv * ld, n, partial, h1, st, nullptr);
+  T *w = V + (int64_t)nv * ld;
+  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h1, w, n, nullptr, pt);
+  k_sum_partials<T><<<1, kB, 0, st>>>(pt, kRedBlocks, 1, nrm, nullptr, scale, h1 + nv, flag);
+  note_launches(2);
+  vec_multidot<T>(V, ld, nv, w, n, partial, h2, st, flag);
+  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h2, w, n, flag, pt);
+  k_sum_partials<T><<<1, kB, 0, st>>>(pt, kRedBlocks, 1, nrm + 1, flag, scale, nullptr, nullptr);
+  note_launches(2);
 }
+template void vec_orthogonalize<float>(float *, int64_t, int, int64_t, double *, double *, double *, double *,
+                                       int *, float *, cudaStream_t);
+template void vec_orthogonalize<double>(double *, int64_t, int, int64_t, double *, double *, double *, double *,
+                                        int *, double *, cudaStream_t);
 
-void vec_normalize(double *w, int64_t n, const double *nrm, const int *flag, cudaStream_t st) {
-  k_normalize<<<grid_n(n), kB, 0, st>>>(w, n, nrm, nrm + 1, flag);
+template <typename T>
+void vec_normalize(T *w, int64_t n, const T *scale, cudaStream_t st) {
+  k_normalize<T><<<grid_n(n / V16<T>::L + 1), kB, 0, st>>>(w, n, scale);
   note_launches(1);
 }
+template void vec_normalize<float>(float *, int64_t, const float *, cudaStream_t);
+template void vec_normalize<double>(double *, int64_t, const double *, cudaStream_t);
 
-void vec_update(const double *V, int64_t ld, int nv, const double *h, double *w, int64_t n, cudaStream_t st) {
-  k_update<<<grid_n(n), kB, 0, st>>>(V, ld, nv, h, w, n);
+template <typename T>
+void vec_sub(const double *b, const T *y, double *r, int64_t n, cudaStream_t st) {
+  k_sub<T><<<grid_n(n), kB, 0, st>>>(b, y, r, n);
   note_launches(1);
 }
-
-void vec_scale_by(const double *x, const double *nrm2_sqrt, double *out, int64_t n, cudaStream_t st) {
-  k_scale_by<<<grid_n(n), kB, 0, st>>>(x, nrm2_sqrt, out, n);
-  note_launches(1);
-}
+template void vec_sub<float>(const double *, const float *, double *, int64_t, cudaStream_t);
+template void vec_sub<double>(const double *, const double *, double *, int64_t, cudaStream_t);
 
 template <typename A, typename B>
 void vec_convert(const A *x, B *y, int64_t n, double a, cudaStream_t st) {
@@ -352,6 +379,7 @@ void vec_convert(const A *x, B *y, int64_t n, double a, cudaStream_t st) {
 template void vec_convert<float, double>(const float *, double *, int64_t, double, cudaStream_t);
 template void vec_convert<double, float>(const double *, float *, int64_t, double, cudaStream_t);
 template void vec_convert<double, double>(const double *, double *, int64_t, double, cudaStream_t);
+template void vec_convert<float, float>(const float *, float *, int64_t, double, cudaStream_t);
 
 template <typename T>
 void vec_combine(const T *Z, int64_t ld, int nz, const double *c, double *x, int64_t n, cudaStream_t st) {
@@ -399,11 +427,11 @@ template void invert_blocks<float>(float *, int64_t, int, int *, cudaStream_t);
 template void invert_blocks<double>(double *, int64_t, int, int *, cudaStream_t);
 
 template <typename T>
-void block_apply(const T *Binv, const double *v, T *z, int64_t n_nodes, int nf, cudaStream_t st) {
+void block_apply(const T *Binv, const T *v, T *z, int64_t n_nodes, int nf, cudaStream_t st) {
   if (nf == 5) { k_block_apply<T, 5><<<grid_n(n_nodes), kB, 0, st>>>(Binv, v, z, n_nodes); note_launches(1); }
   else { k_block_apply<T, 6><<<grid_n(n_nodes), kB, 0, st>>>(Binv, v, z, n_nodes); note_launches(1); }
 }
-template void block_apply<float>(const float *, const double *, float *, int64_t, int, cudaStream_t);
+template void block_apply<float>(const float *, const float *, float *, int64_t, int, cudaStream_t);
 template void block_apply<double>(const double *, const double *, double *, int64_t, int, cudaStream_t);
 
 }  // namespace chns

@@ -10,15 +10,27 @@ namespace chns {
 constexpr int kMaxRestart = 64;
 
 int red_blocks();
-// h[i] = V_i . w for i < nv; partial: (nv + 8) * red_blocks() doubles
-void vec_multidot(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial,
-                  double *h, cudaStream_t st);
+// Krylov vectors: V_i at V + i * ld, ld a multiple of kVecAlign elements and
+// V 16-byte aligned (16-byte loads); products and sums in T, the final sum
+// of block partials in double (vector.cu)
+constexpr int64_t kVecAlign = 64;
+inline int64_t vec_ld(int64_t n) { return (n + kVecAlign - 1) / kVecAlign * kVecAlign; }
+
+// h[i] = V_i . w for i < nv; partial: (nv + 8) * red_blocks() doubles;
+// skipped (h = 0) when flag is given and *flag == 0
+template <typename T>
+void vec_multidot(const T *V, int64_t ld, int nv, const T *w, int64_t n, double *partial, double *h,
+                  cudaStream_t st, const int *flag = nullptr);
+// x . y (double)
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st);
-void vec_update(const double *V, int64_t ld, int nv, const double *h, double *w, int64_t n, cudaStream_t st);
-void vec_orthogonalize(double *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
-                       double *nrm, int *flag, cudaStream_t st);
-void vec_normalize(double *w, int64_t n, const double *nrm, const int *flag, cudaStream_t st);
-void vec_scale_by(const double *x, const double *nrm, double *out, int64_t n, cudaStream_t st);
+template <typename T>
+void vec_orthogonalize(T *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
+                       double *nrm, int *flag, T *scale, cudaStream_t st);
+template <typename T>
+void vec_normalize(T *w, int64_t n, const T *scale, cudaStream_t st);
+// r = b - y
+template <typename T>
+void vec_sub(const double *b, const T *y, double *r, int64_t n, cudaStream_t st);
 template <typename A, typename B>
 void vec_convert(const A *x, B *y, int64_t n, double a, cudaStream_t st);
 template <typename T>
@@ -33,6 +45,6 @@ void probe_get(const int32_t *nodes, int64_t cnt, int nf, int f, const T *y, T *
 template <typename T>
 void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, cudaStream_t st);
 template <typename T>
-void block_apply(const T *Binv, const double *v, T *z, int64_t n_nodes, int nf, cudaStream_t st);
+void block_apply(const T *Binv, const T *v, T *z, int64_t n_nodes, int nf, cudaStream_t st);
 
 }  // namespace chns
