@@ -93,8 +93,11 @@ chns_status ensure_events(Workspace &ws, size_t n) {
   return CHNS_OK;
 }
 
+// Hessenberg column slot: h (pass 1), h (pass 2), norms/flag/scale
+constexpr int kHessSlot = kMaxRestart + 8;
+
 chns_status ensure_pinned(Workspace &ws) {
-  if (!ws.hpinned) CHNS_CUDA_TRY(cudaMallocHost(&ws.hpinned, sizeof(double) * 4 * (kMaxRestart + 8)));
+  if (!ws.hpinned) CHNS_CUDA_TRY(cudaMallocHost(&ws.hpinned, sizeof(double) * 8 * kHessSlot));
   return CHNS_OK;
 }
 
@@ -102,7 +105,7 @@ chns_status norm2(chns_mesh *m, const double *x, double *out_host, cudaStream_t 
   Workspace &ws = m->ws;
   int64_t n = m->n_nodes * m->nf;
   TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
-  TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+  TRY(ws.hdev.ensure(sizeof(double) * 8 * kHessSlot));
   TRY(ensure_pinned(ws));
   double *hd = ws.hdev.as<double>();
   vec_dot(x, x, n, ws.red.as<double>(), hd, st);
@@ -112,40 +115,58 @@ chns_status norm2(chns_mesh *m, const double *x, double *out_host, cudaStream_t 
   return CHNS_OK;
 }
 
-// Per-call timing of a group of launches with CUDA events on the stream.
+// Per-call timing of a group of launches with CUDA events on the stream: a
+// ring of event pairs in the workspace; pairs are read once they completed
+// (the Krylov loop runs ahead of the host by one iteration).
 struct Timer {
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  static constexpr int kPairs = 32;
   double ms = 0.0;
   int calls = 0;
-  size_t next = 0;
+  int64_t head = 0, tail = 0;  // pending pairs: [tail, head)
   Workspace *ws = nullptr;
   bool on = false;
-  chns_status begin(cudaStream_t st, cudaEvent_t *a) {
+  chns_status begin(cudaStream_t st, int *slot) {
     if (!on) return CHNS_OK;
-    TRY(ensure_events(*ws, next + 2));
-    *a = ws->ev[next];
-    CHNS_CUDA_TRY(cudaEventRecord(*a, st));
+    if (ws->tev.empty()) {
+      for (int i = 0; i < 2 * kPairs; ++i) {
+        cudaEvent_t e;
+        CHNS_CUDA_TRY(cudaEventCreate(&e));
+        ws->tev.push_back(e);
+      }
+    }
+    if (head - tail == kPairs) {  // ring full: wait for the oldest pair
+      CHNS_CUDA_TRY(cudaEventSynchronize(ws->tev[2 * (tail % kPairs) + 1]));
+      TRY(collect());
+    }
+    *slot = int(head % kPairs);
+    CHNS_CUDA_TRY(cudaEventRecord(ws->tev[2 * *slot], st));
     return CHNS_OK;
   }
-  chns_status end(cudaStream_t st, cudaEvent_t a) {
+  chns_status end(cudaStream_t st, int slot) {
     if (!on) return CHNS_OK;
-    cudaEvent_t b = ws->ev[next + 1];
-    CHNS_CUDA_TRY(cudaEventRecord(b, st));
-    pending.push_back({a, b});
-    next += 2;
+    CHNS_CUDA_TRY(cudaEventRecord(ws->tev[2 * slot + 1], st));
+    ++head;
     return CHNS_OK;
   }
-  // after a stream synchronisation
+  // add the pairs that have completed, oldest first
   chns_status collect() {
-    for (auto &p : pending) {
+    while (tail < head) {
+      const int sl = int(tail % kPairs);
+      cudaError_t q = cudaEventQuery(ws->tev[2 * sl + 1]);
+      if (q == cudaErrorNotReady) break;
+      CHNS_CUDA_TRY(q);
       float t = 0.f;
-      CHNS_CUDA_TRY(cudaEventElapsedTime(&t, p.first, p.second));
+      CHNS_CUDA_TRY(cudaEventElapsedTime(&t, ws->tev[2 * sl], ws->tev[2 * sl + 1]));
       ms += t;
       ++calls;
+      ++tail;
     }
-    pending.clear();
-    next = 0;
     return CHNS_OK;
+  }
+  // after the stream has drained
+  chns_status finish() {
+    if (tail < head) CHNS_CUDA_TRY(cudaEventSynchronize(ws->tev[2 * ((head - 1) % kPairs) + 1]));
+    return collect();
   }
 };
 
@@ -182,12 +203,36 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
   return check_launch();
 }
 
+// What an Arnoldi-step graph bakes in: buffers, sizes, coarse-space state and
+// the element coefficients (kernel arguments by value)
+struct StepKey {
+  const void *p[13];
+  int64_t i[5];
+  PhysCoef pc;
+};
+
+// CHNS_NO_GRAPHS=1 launches the Arnoldi steps kernel by kernel
+bool use_graphs() {
+  static int on = -1;
+  if (on < 0) {
+    const char *e = std::getenv("CHNS_NO_GRAPHS");
+    on = (e && *e && *e != '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
 // ---------------------------------------------------------------- FGMRES
 // Solve J x = b (b = -F) with right-preconditioned flexible GMRES(m).  The
 // basis V, the preconditioned directions Z, J.z and the Gram-Schmidt
 // (classical, a second pass on severe cancellation) are in the element
 // precision T, with double accumulation of the dot products; the Hessenberg
 // least squares, x, r = b - J x and its norm are in double.
+//
+// The host needs column j of the Hessenberg matrix only for the Givens
+// rotations and the convergence test, so Arnoldi step j + 1 is queued on the
+// stream before the host waits for column j (two result slots, a pinned
+// mirror each): the GPU never idles on the host.  When step j converges,
+// the queued step j + 1 is discarded.
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
                    const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
@@ -197,19 +242,20 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   const int64_t n = m->n_nodes * nf;
   const int mr = o.krylov_restart;
   const int64_t ld = vec_ld(n);  // basis stride: 16-byte aligned vectors
+  constexpr int K = kHessSlot;
   TRY(ws.V.ensure(sizeof(T) * (mr + 1) * ld));
   TRY(ws.Z.ensure(sizeof(T) * mr * ld));
   TRY(ws.r.ensure(sizeof(double) * n));
   TRY(ws.wv.ensure(sizeof(T) * n));
   TRY(ws.yv.ensure(sizeof(T) * n));
   TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
-  TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+  TRY(ws.hdev.ensure(sizeof(double) * 8 * K));
   TRY(ensure_pinned(ws));
+  TRY(ensure_events(ws, 2));
   double *r = ws.r.as<double>();
   T *V = ws.V.as<T>(), *Z = ws.Z.as<T>(), *yv = ws.yv.as<T>(), *tv = ws.wv.as<T>();
-  double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>(), *hp = ws.hpinned;
-  double *h1 = hd, *h2 = hd + (kMaxRestart + 8), *nr = hd + 2 * (kMaxRestart + 8);
-  double *cz = hd + 3 * (kMaxRestart + 8);
+  double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>();
+  double *cz = hd + 6 * K;
 
   CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
   CHNS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -220,6 +266,96 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   if (beta0 == 0.0) return CHNS_OK;
   const double target = o.krylov_rtol * beta0;
   double beta = beta0;
+
+  // Arnoldi step j: z_j = M^{-1} v_j, w = J z_j orthogonalised against
+  // v_0..v_j and normalised into v_{j+1}; column j to pinned slot j % 2.
+  // Launched on stream s; with `cap` (stream capture) the J.w bracket is
+  // recorded as external events of the graph.
+  Workspace::StepGraphs &G = ws.kg[sizeof(T) == 8 ? 1 : 0];
+  auto arnoldi_body = [&](int j, cudaStream_t s, bool cap) -> chns_status {
+    const int sl = j & 1;
+    double *h1 = hd + 3 * K * sl, *h2 = h1 + K, *nr = h1 + 2 * K;
+    T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
+    T *zj = Z + (int64_t)j * ld;
+    precond_apply<T>(m, Binv, coarse, vj, zj, s);
+    int ev = 0;
+    if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j], s, cudaEventRecordExternal));
+    else TRY(tj.begin(s, &ev));
+    TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, w, s));
+    if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j + 1], s, cudaEventRecordExternal));
+    else TRY(tj.end(s, ev));
+    int *flag = reinterpret_cast<int *>(nr + 2);
+    T *scale = reinterpret_cast<T *>(nr + 3);
+    vec_orthogonalize<T>(V, ld, j + 1, n, part, h1, h2, nr, flag, scale, s);
+    vec_normalize<T>(w, n, scale, s);
+    CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned + 3 * K * sl, h1, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost, s));
+    return CHNS_OK;
+  };
+  // Arnoldi steps as CUDA graphs (one per j, captured at first use): a step
+  // is ~25 launches of mostly short kernels, and host launch cost, not the
+  // GPU, bounds a step launched one kernel at a time
+  const bool graphs = use_graphs();
+  if (graphs) {
+    StepKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.p[0] = V; key.p[1] = Z; key.p[2] = ut; key.p[3] = dl; key.p[4] = Binv; key.p[5] = part;
+    key.p[6] = hd; key.p[7] = ws.hpinned; key.p[8] = m->coarse.vec.as<void>();
+    key.p[9] = m->coarse.rpart.as<void>(); key.p[10] = m->coarse.M.as<void>();
+    key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes;
+    key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
+    key.pc = pc;
+    const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
+    if (G.key.size() != sizeof(key) || std::memcmp(G.key.data(), kb, sizeof(key)) != 0) {
+      G.clear();
+      G.key.assign(kb, kb + sizeof(key));
+    }
+    if ((int)G.exec.size() < mr) {
+      G.exec.resize(mr, nullptr);
+      G.launches.resize(mr, 0);
+    }
+    while ((int)G.jv.size() < 2 * mr) {
+      cudaEvent_t e;
+      CHNS_CUDA_TRY(cudaEventCreate(&e));
+      G.jv.push_back(e);
+    }
+    if (!ws.cap) CHNS_CUDA_TRY(cudaStreamCreateWithFlags(&ws.cap, cudaStreamNonBlocking));
+  }
+  auto capture = [&](int j) -> chns_status {
+    int cnt = 0;
+    set_capture_sink(&cnt);
+    cudaError_t e = cudaStreamBeginCapture(ws.cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_capture_sink(nullptr);
+      CHNS_CUDA_TRY(e);
+    }
+    chns_status sb = arnoldi_body(j, ws.cap, true);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(ws.cap, &gr);
+    set_capture_sink(nullptr);
+    if (sb != CHNS_OK || e != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      if (sb != CHNS_OK) return sb;
+      CHNS_CUDA_TRY(e);
+    }
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, gr, 0);
+    cudaGraphDestroy(gr);
+    CHNS_CUDA_TRY(e);
+    G.exec[j] = ge;
+    G.launches[j] = cnt;
+    return CHNS_OK;
+  };
+  auto arnoldi = [&](int j) -> chns_status {
+    if (graphs) {
+      if (!G.exec[j]) TRY(capture(j));
+      CHNS_CUDA_TRY(cudaGraphLaunch(G.exec[j], st));
+      note_launches(G.launches[j]);
+    } else {
+      TRY(arnoldi_body(j, st, false));
+    }
+    CHNS_CUDA_TRY(cudaEventRecord(ws.ev[j & 1], st));
+    return CHNS_OK;
+  };
   std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), yk(mr);
   int total = 0;
   while (true) {
@@ -230,27 +366,22 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     int j_end = 0;
     bool done = false;
     for (int j = 0; j < mr; ++j) {
-      T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
-      T *zj = Z + (int64_t)j * ld;
-      precond_apply<T>(m, Binv, coarse, vj, zj, st);
-      cudaEvent_t e0 = nullptr;
-      TRY(tj.begin(st, &e0));
-      TRY(jacvec_prepared<T>(m, pc, ut, dl, zj, w, st));
-      TRY(tj.end(st, e0));
-      // classical Gram-Schmidt, a second pass only when the DGKS test asks;
-      // V_{j+1} normalised on the device
-      int *flag = reinterpret_cast<int *>(nr + 2);
-      T *scale = reinterpret_cast<T *>(nr + 3);
-      vec_orthogonalize<T>(V, ld, j + 1, n, part, h1, h2, nr, flag, scale, st);
-      vec_normalize<T>(w, n, scale, st);
-      CHNS_CUDA_TRY(cudaMemcpyAsync(hp, hd, sizeof(double) * 3 * (kMaxRestart + 8), cudaMemcpyDeviceToHost, st));
-      CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (j == 0) TRY(arnoldi(0));
+      if (j + 1 < mr && total + 1 < o.krylov_max_it) TRY(arnoldi(j + 1));  // queued ahead
+      CHNS_CUDA_TRY(cudaEventSynchronize(ws.ev[j & 1]));
+      if (graphs && tj.on) {
+        float t = 0.f;
+        CHNS_CUDA_TRY(cudaEventElapsedTime(&t, G.jv[2 * j], G.jv[2 * j + 1]));
+        tj.ms += t;
+        ++tj.calls;
+      }
       TRY(tj.collect());
-      const double *hnr = hp + 2 * (kMaxRestart + 8);
+      const double *hp = ws.hpinned + 3 * K * (j & 1);
+      const double *hnr = hp + 2 * K;
       const int hflag = *reinterpret_cast<const int *>(hnr + 2);
       double hn = std::sqrt(hflag ? hnr[1] : hnr[0]);
       if (!std::isfinite(hn)) { set_error("non-finite Krylov vector"); return CHNS_ERR_NONFINITE; }
-      for (int i = 0; i <= j; ++i) H[i * mr + j] = hp[i] + (hflag ? hp[(kMaxRestart + 8) + i] : 0.0);
+      for (int i = 0; i <= j; ++i) H[i * mr + j] = hp[i] + (hflag ? hp[K + i] : 0.0);
       H[(j + 1) * mr + j] = hn;
       // Givens rotations
       for (int i = 0; i < j; ++i) {
@@ -283,10 +414,10 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     if (done || total >= o.krylov_max_it) break;
     // restart: r = b - J x
     vec_convert<double, T>(x, tv, n, 1.0, st);
-    cudaEvent_t e0 = nullptr;
-    TRY(tj.begin(st, &e0));
+    int ev = 0;
+    TRY(tj.begin(st, &ev));
     TRY(jacvec_prepared<T>(m, pc, ut, dl, tv, yv, st));
-    TRY(tj.end(st, e0));
+    TRY(tj.end(st, ev));
     vec_sub<T>(b, yv, r, n, st);
     TRY(norm2(m, r, &beta, st));
     TRY(tj.collect());
@@ -294,6 +425,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     if (beta <= target) break;
   }
   *its_out = total;
+  TRY(tj.finish());
   return check_launch();
 }
 
@@ -401,7 +533,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   auto instance_norms = [&]() -> chns_status {
     if (ni == 1) return CHNS_OK;
     TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
-    TRY(ws.hdev.ensure(sizeof(double) * std::max<int64_t>(4 * (kMaxRestart + 8), ni + 8)));
+    TRY(ws.hdev.ensure(sizeof(double) * std::max<int64_t>(8 * kHessSlot, ni + 8)));
     double *hd = ws.hdev.as<double>();
     for (int q = 0; q < ni; ++q) {
       const int64_t a = m->inst_node_start[q] * nf, b = m->inst_node_start[q + 1] * nf;
@@ -686,7 +818,7 @@ chns_status chns_init_mu(const chns_mesh *mc, const chns_params *p, double *U, v
     vec_mask_field(q, m->n_nodes, nf, imu, -2.0, st);
     double pq = 0.0;
     TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
-    TRY(ws.hdev.ensure(sizeof(double) * 4 * (kMaxRestart + 8)));
+    TRY(ws.hdev.ensure(sizeof(double) * 8 * kHessSlot));
     vec_dot(pv, q, n, ws.red.as<double>(), ws.hdev.as<double>(), st);
     CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, ws.hdev.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, st));
     CHNS_CUDA_TRY(cudaStreamSynchronize(st));

@@ -13,6 +13,7 @@ namespace chns {
 
 void set_error(const char *fmt, ...);
 void note_launches(int n);  // tracing counter of kernel launches
+void set_capture_sink(int *sink);  // while set, this thread's launches count into *sink
 
 #define CHNS_CUDA_TRY(expr)                                                      \
   do {                                                                           \
@@ -63,7 +64,19 @@ struct Workspace {
   int pc_steps_left = 0;
   int pc_precision = -1, pc_coarse = -1;
   chns_params pc_params{};
-  std::vector<cudaEvent_t> ev;
+  // CUDA graphs of the Arnoldi steps, one per step index and element
+  // precision (0 float, 1 double), valid while `key` (the pointers and
+  // parameters they were captured with) is unchanged
+  struct StepGraphs {
+    std::vector<cudaGraphExec_t> exec;
+    std::vector<int> launches;         // kernel launches per replay
+    std::vector<cudaEvent_t> jv;       // J.w start/end event of each step
+    std::vector<unsigned char> key;
+    void clear();
+  } kg[2];
+  cudaStream_t cap = nullptr;          // capture stream
+  std::vector<cudaEvent_t> ev;         // general events (Krylov column slots 0, 1; residual timing)
+  std::vector<cudaEvent_t> tev;        // J.w timing ring
   ~Workspace();
 };
 

@@ -30,7 +30,12 @@ const char *last_error() { return g_last_error.c_str(); }
 namespace {
 std::atomic<uint64_t> g_launches{0};
 }
-void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+thread_local int *t_capture_sink = nullptr;
+void note_launches(int n) {
+  if (t_capture_sink) *t_capture_sink += n;  // captured into a graph: counted per replay
+  else g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed);
+}
+void set_capture_sink(int *sink) { t_capture_sink = sink; }
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 chns_status DevBuf::ensure(size_t n) {
@@ -53,8 +58,22 @@ void DevBuf::release() {
   bytes = 0;
 }
 
+void Workspace::StepGraphs::clear() {
+  for (auto g : exec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto e : jv) cudaEventDestroy(e);
+  exec.clear();
+  launches.clear();
+  jv.clear();
+  key.clear();
+}
+
 Workspace::~Workspace() {
+  kg[0].clear();
+  kg[1].clear();
+  if (cap) cudaStreamDestroy(cap);
   for (auto e : ev) cudaEventDestroy(e);
+  for (auto e : tev) cudaEventDestroy(e);
   if (hpinned) cudaFreeHost(hpinned);
 }
 

@@ -89,38 +89,43 @@ __global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int n
   }
 }
 
-// partial sums of V_{i0+k} . w, k < nv <= NV; V_i at V + i * ld with ld a
-// multiple of 16 bytes / sizeof(T) and V 16-byte aligned; skipped when flag
-// is given and *flag == 0
-template <typename T, int NV>
-__global__ void __launch_bounds__(kB) k_multidot(const T *__restrict__ V, int64_t ld, int i0, int nv,
+// partial sums of V_k . w for all k < nv, eight vectors at a time (w is
+// re-read per group, from L2); V_i at V + i * ld with ld a multiple of 16
+// bytes / sizeof(T) and V 16-byte aligned; skipped when flag is given and
+// *flag == 0
+template <typename T>
+__global__ void __launch_bounds__(kB) k_multidot(const T *__restrict__ V, int64_t ld, int nv,
                                                  const T *__restrict__ w, int64_t n, T *__restrict__ partial,
                                                  const int *__restrict__ flag) {
   if (flag && *flag == 0) return;
-  constexpr int L = V16<T>::L;
-  T acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = T(0);
+  constexpr int L = V16<T>::L, NV = 8;
   const int64_t nl = n / L;
   const V16<T> *wv = reinterpret_cast<const V16<T> *>(w);
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nl; t += int64_t(gridDim.x) * kB) {
-    const V16<T> x = wv[t];
+  for (int i0 = 0; i0 < nv; i0 += NV) {
+    const int c = nv - i0;
+    T acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) {
-        const V16<T> a = reinterpret_cast<const V16<T> *>(V + (int64_t)(i0 + k) * ld)[t];
+    for (int k = 0; k < NV; ++k) acc[k] = T(0);
+    for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nl; t += int64_t(gridDim.x) * kB) {
+      const V16<T> x = wv[t];
 #pragma unroll
-        for (int l = 0; l < L; ++l) acc[k] = fma(a.a[l], x.a[l], acc[k]);
-      }
+      for (int k = 0; k < NV; ++k)
+        if (k < c) {
+          const V16<T> a = reinterpret_cast<const V16<T> *>(V + (int64_t)(i0 + k) * ld)[t];
+#pragma unroll
+          for (int l = 0; l < L; ++l) acc[k] = fma(a.a[l], x.a[l], acc[k]);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - nl * L) {
+      const int64_t t = nl * L + threadIdx.x;
+      const T x = w[t];
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k < c) acc[k] = fma(V[(int64_t)(i0 + k) * ld + t], x, acc[k]);
+    }
+    block_sum_store<T, NV>(acc, partial + (int64_t)i0 * gridDim.x);
+    __syncthreads();  // the block-sum scratch is reused by the next group
   }
-  if (blockIdx.x == 0 && threadIdx.x < n - nl * L) {
-    const int64_t t = nl * L + threadIdx.x;
-    const T x = w[t];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) acc[k] = fma(V[(int64_t)(i0 + k) * ld + t], x, acc[k]);
-  }
-  block_sum_store<T, NV>(acc, partial + (int64_t)i0 * gridDim.x);
 }
 
 // w -= sum_i h[i] V_i (i < nv) and block partial sums of the new |w|^2;
@@ -310,13 +315,9 @@ template <typename T>
 void vec_multidot(const T *V, int64_t ld, int nv, const T *w, int64_t n, double *partial, double *h,
                   cudaStream_t st, const int *flag) {
   T *pt = reinterpret_cast<T *>(partial);
-  for (int i0 = 0; i0 < nv; i0 += 8) {
-    int c = std::min(8, nv - i0);
-    k_multidot<T, 8><<<kRedBlocks, kB, 0, st>>>(V, ld, i0, c, w, n, pt, flag);
-    note_launches(1);
-  }
+  k_multidot<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, w, n, pt, flag);
   k_sum_partials<T><<<nv, kB, 0, st>>>(pt, kRedBlocks, nv, h, flag, nullptr, nullptr, nullptr);
-  note_launches(1);
+  note_launches(2);
 }
 template void vec_multidot<float>(const float *, int64_t, int, const float *, int64_t, double *, double *,
                                   cudaStream_t, const int *);
