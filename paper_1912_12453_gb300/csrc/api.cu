@@ -16,6 +16,7 @@ namespace chns {
 chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor, int max_level,
                        const double lo[3], const double hi[3], chns_mesh *m);
 chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u);
+chns_status build_gather(chns_mesh *m);
 const char *last_error();
 uint64_t launches();
 }  // namespace chns
@@ -75,12 +76,21 @@ chns_status residual_prepared(chns_mesh *m, const PhysCoef &pc, const double *Un
   return check_launch();
 }
 
+// element-local J.w buffer of precision T (n_elem * 2^dim * nf values)
+template <typename T>
+chns_status ensure_ebuf(chns_mesh *m, T **E) {
+  DevBuf &b = sizeof(T) == 8 ? m->ws.e64 : m->ws.e32;
+  TRY(b.ensure(sizeof(T) * (m->n_elem << m->dim) * m->nf));
+  *E = b.as<T>();
+  return CHNS_OK;
+}
+
 template <typename T>
 chns_status jacvec_prepared(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *y,
                             cudaStream_t st) {
-  CHNS_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(T) * m->n_nodes * m->nf, st));
-  launch_jacvec<T>(m, pc, ut, dl, w, y, st);
-  launch_dirichlet_jv<T>(m, w, y, st);
+  T *E = nullptr;
+  TRY(ensure_ebuf<T>(m, &E));
+  launch_jacvec<T>(m, pc, ut, dl, w, E, y, st);
   return check_launch();
 }
 
@@ -206,7 +216,7 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
 // What an Arnoldi-step graph bakes in: buffers, sizes, coarse-space state and
 // the element coefficients (kernel arguments by value)
 struct StepKey {
-  const void *p[13];
+  const void *p[14];
   int64_t i[5];
   PhysCoef pc;
 };
@@ -295,13 +305,15 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   // is ~25 launches of mostly short kernels, and host launch cost, not the
   // GPU, bounds a step launched one kernel at a time
   const bool graphs = use_graphs();
+  T *Ebuf = nullptr;
+  TRY(ensure_ebuf<T>(m, &Ebuf));
   if (graphs) {
     StepKey key;
     std::memset(&key, 0, sizeof(key));
     key.p[0] = V; key.p[1] = Z; key.p[2] = ut; key.p[3] = dl; key.p[4] = Binv; key.p[5] = part;
     key.p[6] = hd; key.p[7] = ws.hpinned; key.p[8] = m->coarse.vec.as<void>();
     key.p[9] = m->coarse.rpart.as<void>(); key.p[10] = m->coarse.M.as<void>();
-    key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes;
+    key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
@@ -708,6 +720,7 @@ chns_status chns_mesh_create(int dim, int64_t n_leaves, const uint8_t *level, co
   *out = nullptr;
   chns_mesh *m = new chns_mesh;
   chns_status s = build_mesh(dim, n_leaves, level, anchor, max_level, lo, hi, m);
+  if (s == CHNS_OK) s = build_gather(m);
   if (s != CHNS_OK) {
     chns_mesh_destroy(m);
     return s;
@@ -743,6 +756,9 @@ void chns_mesh_destroy(chns_mesh *m) {
   cudaFree(m->hang);
   cudaFree(m->wall);
   cudaFree(m->node_perm);
+  cudaFree(m->gptr);
+  cudaFree(m->gent);
+  cudaFree(m->nflag);
   cudaFree(m->pins);
   cudaFree(m->elem_inst);
   cudaFree(m->node_inst);
@@ -752,6 +768,7 @@ void chns_mesh_destroy(chns_mesh *m) {
   m->ws.ut.release(); m->ws.dl.release(); m->ws.ut32.release(); m->ws.dl32.release(); m->ws.f.release();
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
+  m->ws.e32.release(); m->ws.e64.release();
   delete m;
   cudaSetDevice(prev);
 }
@@ -876,6 +893,7 @@ chns_status chns_batch_create(int n, chns_mesh *const *meshes, const chns_params
     if (ms.empty()) continue;
     g.u = new chns_mesh;
     chns_status s = build_union(ms, g.u);
+    if (s == CHNS_OK) s = build_gather(g.u);
     if (s == CHNS_OK) s = upload_coef_tables(g.u, pcs, nullptr);
     if (s != CHNS_OK) {
       chns_mesh_destroy(g.u);

@@ -54,6 +54,7 @@ struct Workspace {
   DevBuf V;                            // double (m+1) n_dof Krylov basis
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors
+  DevBuf e32, e64;                     // element-local J.w contributions (n_elem * 2^dim * nf)
   DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks (element precision)
   DevBuf binv64;                       // the same blocks in double (FP64 J.w iterations)
   DevBuf red;                          // reduction partials
@@ -138,6 +139,13 @@ struct chns_mesh {
   int32_t *hang = nullptr;             // n_hang * 4 parent nodes (-1 padded for edge midpoints)
   int32_t *wall = nullptr;             // n_wall node indices on the box boundary
   int32_t *node_perm = nullptr;        // n_nodes node indices grouped by node colour
+  // node gather of element-local J.w contributions: the (element, corner)
+  // slots feeding node i are gent[gptr[i] .. gptr[i+1]), each slot e*nc+c
+  // with its hanging-node weight in the top two bits (0: 1, 1: 1/2, 2: 1/4),
+  // in increasing slot order; nflag: bit 0 wall node, bit 1 pinned pressure
+  int32_t *gptr = nullptr;             // n_nodes + 1
+  int32_t *gent = nullptr;
+  uint8_t *nflag = nullptr;            // n_nodes
   int device = 0;
   chns::Workspace ws;
   chns::Coarse coarse;

@@ -209,6 +209,24 @@ __device__ __forceinline__ void add_block(O *__restrict__ p, const T *r, T wgt) 
   }
 }
 
+template <int N, typename T>
+__device__ __forceinline__ void store_block(T *__restrict__ p, const T *r) {
+  if constexpr (N % 2 == 0) {
+    using P = typename Pair<T>::type;
+    P *q = reinterpret_cast<P *>(p);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      P v;
+      v.x = r[2 * k];
+      v.y = r[2 * k + 1];
+      q[k] = v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) p[k] = r[k];
+  }
+}
+
 // non-atomic: elements of one launch (one colour) touch disjoint nodes
 template <int N, typename T, typename O>
 __device__ __forceinline__ void scatter(int cn, const int32_t *__restrict__ hang, O *__restrict__ dst,
@@ -491,6 +509,12 @@ __global__ void __launch_bounds__(256, 3) k_element(
       r[k] = contract<D>(W * Sq[k].d, Vk, s);
     }
   }
+  if (MODE == 1) {
+    // J.w: element-local output, slot (e, corner); k_gather_nodes sums the
+    // slots of each node in a fixed order
+    if (active) store_block<NF>(reinterpret_cast<T *>(out) + (e * NC + lc) * NF, r);
+    return;
+  }
   // Lanes of one element may reach the same node: a hanging corner's parents
   // can be corners of the element or parents of its other hanging corner.
   // Warps that hold a hanging corner scatter one corner index at a time.
@@ -529,6 +553,39 @@ __global__ void k_cast(const double *__restrict__ x, int64_t n, T *__restrict__ 
     y[i] = T(x[i]);
 }
 
+// y[i] = sum over the slots of node i of weight * E[slot] (fixed order), then
+// the constrained rows: y = w on wall velocities and the pinned pressure
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_gather_nodes(const int32_t *__restrict__ gptr,
+                                                      const int32_t *__restrict__ gent,
+                                                      const uint8_t *__restrict__ nflag, int64_t n_nodes,
+                                                      const T *__restrict__ E, const T *__restrict__ w,
+                                                      T *__restrict__ y) {
+  constexpr int NF = D + 3;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_nodes; i += int64_t(gridDim.x) * blockDim.x) {
+    T acc[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) acc[k] = T(0);
+    const int p1 = gptr[i + 1];
+    for (int p = gptr[i]; p < p1; ++p) {
+      const uint32_t ent = uint32_t(gent[p]);
+      const int64_t slot = int64_t(ent & 0x3fffffffu);
+      const uint32_t code = ent >> 30;
+      const T wt = code == 0 ? T(1) : (code == 1 ? T(0.5) : T(0.25));
+      T v[NF];
+      load_block<NF>(E + slot * NF, v);
+#pragma unroll
+      for (int k = 0; k < NF; ++k) acc[k] = fma(wt, v[k], acc[k]);
+    }
+    const uint8_t fl = nflag[i];
+    if (fl & 1)
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = w[i * NF + k];
+    if (fl & 2) acc[D] = w[i * NF + D];
+    store_block<NF>(y + i * NF, acc);
+  }
+}
+
 // constrained rows of the residual: wall velocities and the pinned pressure
 __global__ void k_dirichlet_res(const int32_t *__restrict__ wall, int64_t n_wall, const int32_t *__restrict__ pins,
                                 int64_t n_pins, int dim, const double *__restrict__ Un,
@@ -542,21 +599,6 @@ __global__ void k_dirichlet_res(const int32_t *__restrict__ wall, int64_t n_wall
   if (i < n_pins) {
     int64_t b = int64_t(pins[i]) * nf + dim;
     F[b] = Un[b] - (bc ? bc[b] : 0.0);
-  }
-}
-
-template <typename T>
-__global__ void k_dirichlet_jv(const int32_t *__restrict__ wall, int64_t n_wall, const int32_t *__restrict__ pins,
-                               int64_t n_pins, int dim, const T *__restrict__ w, T *__restrict__ y) {
-  const int nf = dim + 3;
-  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i < n_wall) {
-    int64_t b = int64_t(wall[i]) * nf;
-    for (int k = 0; k < dim; ++k) y[b + k] = w[b + k];
-  }
-  if (i < n_pins) {
-    int64_t b = int64_t(pins[i]) * nf + dim;
-    y[b] = w[b];
   }
 }
 
@@ -711,31 +753,36 @@ void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, c
   }
 }
 
+// J.w in two launches: all elements at once into the element-local buffer E
+// (n_elem * 2^dim * nf values of T), then the node gather with the
+// constrained rows (no colouring, no output zeroing)
 template <typename T>
-void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *y,
+void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *E, T *y,
                    cudaStream_t st) {
-  if (m->dim == 2) element_pass<2, T, 1, false, T>(m, pc, ut, dl, w, nullptr, y, st, 0, m->n_colours);
-  else element_pass<3, T, 1, false, T>(m, pc, ut, dl, w, nullptr, y, st, 0, m->n_colours);
+  KCoef<T> c = kcoef<T>(pc);
+  const KCoef<T> *tab = reinterpret_cast<const KCoef<T> *>(sizeof(T) == 8 ? m->coef64 : m->coef32);
+  const unsigned gn = grid_nodes(m->n_nodes);
+  if (m->dim == 2) {
+    k_element<2, T, 1, false, T><<<grid_for(m->n_elem << 2), kBlock, 0, st>>>(
+        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, w, nullptr, E, c, tab, m->elem_inst);
+    k_gather_nodes<2, T><<<gn, kBlock, 0, st>>>(m->gptr, m->gent, m->nflag, m->n_nodes, E, w, y);
+  } else {
+    k_element<3, T, 1, false, T><<<grid_for(m->n_elem << 3), kBlock, 0, st>>>(
+        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, w, nullptr, E, c, tab, m->elem_inst);
+    k_gather_nodes<3, T><<<gn, kBlock, 0, st>>>(m->gptr, m->gent, m->nflag, m->n_nodes, E, w, y);
+  }
+  note_launches(2);
 }
 template void launch_jacvec<float>(const chns_mesh *, const PhysCoef &, const float *, const float *,
-                                   const float *, float *, cudaStream_t);
+                                   const float *, float *, float *, cudaStream_t);
 template void launch_jacvec<double>(const chns_mesh *, const PhysCoef &, const double *, const double *,
-                                    const double *, double *, cudaStream_t);
+                                    const double *, double *, double *, cudaStream_t);
 
 void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st) {
   int64_t n = std::max<int64_t>(std::max(m->n_wall, m->n_pins), 1);
   k_dirichlet_res<<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->pins, m->n_pins, m->dim, Un, bc, F);
   note_launches(1);
 }
-
-template <typename T>
-void launch_dirichlet_jv(const chns_mesh *m, const T *w, T *y, cudaStream_t st) {
-  int64_t n = std::max<int64_t>(std::max(m->n_wall, m->n_pins), 1);
-  k_dirichlet_jv<T><<<grid_for(n), kBlock, 0, st>>>(m->wall, m->n_wall, m->pins, m->n_pins, m->dim, w, y);
-  note_launches(1);
-}
-template void launch_dirichlet_jv<float>(const chns_mesh *, const float *, float *, cudaStream_t);
-template void launch_dirichlet_jv<double>(const chns_mesh *, const double *, double *, cudaStream_t);
 
 chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, cudaStream_t st) {
   const size_t n = pcs.size();

@@ -17,11 +17,9 @@ void launch_cast(const double *x, int64_t n, T *y, cudaStream_t st);
 void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
                      const double *f, double *F, cudaStream_t st);
 template <typename T>
-void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *y,
+void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *E, T *y,
                    cudaStream_t st);
 void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st);
-template <typename T>
-void launch_dirichlet_jv(const chns_mesh *m, const T *w, T *y, cudaStream_t st);
 int64_t energy_blocks(const chns_mesh *m);
 // per-instance element coefficients of a batched (union) mesh
 chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, cudaStream_t st);

@@ -502,6 +502,48 @@ std::vector<T> download(const T *d, size_t n) {
   return h;
 }
 
+// Node gather lists of a built mesh (single or union): for every node, the
+// (element, corner) slots whose element-local J.w contribution it receives,
+// directly (weight 1) or as a parent of a hanging corner (1/2 on an edge,
+// 1/4 on a face), in increasing slot order so that the sums are taken in a
+// fixed order; and the constrained-row flags of the nodes.
+chns_status build_gather(chns_mesh *m) {
+  const int nc = 1 << m->dim;
+  const int64_t ns = m->n_elem * nc;
+  if (ns >= (int64_t(1) << 30)) { set_error("mesh too large for the node gather"); return CHNS_ERR_ARG; }
+  const std::vector<int32_t> conn = download(m->conn, size_t(ns));
+  const std::vector<int32_t> hang = download(m->hang, size_t(m->n_hang) * 4);
+  const std::vector<int32_t> wall = download(m->wall, size_t(m->n_wall));
+  const std::vector<int32_t> pins = download(m->pins, size_t(m->n_pins));
+  std::vector<int64_t> cnt(size_t(m->n_nodes) + 1, 0);
+  auto each = [&](auto &&fn) {
+    for (int64_t s = 0; s < ns; ++s) {
+      const int32_t v = conn[s];
+      if (v >= 0) {
+        fn(v, s, 0);
+      } else {
+        const int32_t *p = &hang[size_t(-v - 1) * 4];
+        const int code = p[2] < 0 ? 1 : 2;
+        for (int k = 0; k < (p[2] < 0 ? 2 : 4); ++k) fn(p[k], s, code);
+      }
+    }
+  };
+  each([&](int32_t i, int64_t, int) { cnt[size_t(i) + 1]++; });
+  for (int64_t i = 0; i < m->n_nodes; ++i) cnt[i + 1] += cnt[i];
+  if (cnt[m->n_nodes] >= (int64_t(1) << 31)) { set_error("mesh too large for the node gather"); return CHNS_ERR_ARG; }
+  std::vector<int32_t> gptr(cnt.begin(), cnt.end()), gent(size_t(cnt[m->n_nodes]));
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  each([&](int32_t i, int64_t s, int code) { gent[fill[i]++] = int32_t(uint32_t(s) | (uint32_t(code) << 30)); });
+  std::vector<uint8_t> nflag(size_t(m->n_nodes), 0);
+  for (int32_t i : wall) nflag[i] |= 1;
+  for (int32_t i : pins) nflag[i] |= 2;
+  chns_status st;
+  if ((st = upload(&m->gptr, gptr)) != CHNS_OK) return st;
+  if ((st = upload(&m->gent, gent)) != CHNS_OK) return st;
+  if ((st = upload(&m->nflag, nflag)) != CHNS_OK) return st;
+  return CHNS_OK;
+}
+
 // One mesh holding several independent problems of the same dimension: the
 // instances' nodes and elements are concatenated (instance order), element
 // colour c of the union is colour c of every instance (instances share no
