@@ -216,7 +216,7 @@ chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, co
 // What an Arnoldi-step graph bakes in: buffers, sizes, coarse-space state and
 // the element coefficients (kernel arguments by value)
 struct StepKey {
-  const void *p[14];
+  const void *p[15];
   int64_t i[5];
   PhysCoef pc;
 };
@@ -266,6 +266,10 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   T *V = ws.V.as<T>(), *Z = ws.Z.as<T>(), *yv = ws.yv.as<T>(), *tv = ws.wv.as<T>();
   double *part = ws.red.as<double>(), *hd = ws.hdev.as<double>();
   double *cz = hd + 6 * K;
+  // grid-reduction ticket of the Gram-Schmidt kernels (zero between launches)
+  TRY(ws.ctr.ensure(64));
+  unsigned *ctr = ws.ctr.as<unsigned>();
+  CHNS_CUDA_TRY(cudaMemsetAsync(ctr, 0, 64, st));
 
   CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
   CHNS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -296,7 +300,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     else TRY(tj.end(s, ev));
     int *flag = reinterpret_cast<int *>(nr + 2);
     T *scale = reinterpret_cast<T *>(nr + 3);
-    vec_orthogonalize<T>(V, ld, j + 1, n, part, h1, h2, nr, flag, scale, s);
+    vec_orthogonalize<T>(V, ld, j + 1, n, part, h1, h2, nr, flag, scale, ctr, s);
     vec_normalize<T>(w, n, scale, s);
     CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned + 3 * K * sl, h1, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost, s));
     return CHNS_OK;
@@ -314,6 +318,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     key.p[6] = hd; key.p[7] = ws.hpinned; key.p[8] = m->coarse.vec.as<void>();
     key.p[9] = m->coarse.rpart.as<void>(); key.p[10] = m->coarse.M.as<void>();
     key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
+    key.p[14] = ctr;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);

@@ -55,6 +55,7 @@ struct Workspace {
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors
   DevBuf e32, e64;                     // element-local J.w contributions (n_elem * 2^dim * nf)
+  DevBuf ctr;                          // grid-reduction tickets
   DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks (element precision)
   DevBuf binv64;                       // the same blocks in double (FP64 J.w iterations)
   DevBuf red;                          // reduction partials

@@ -201,7 +201,7 @@ __global__ void k_gather_sum(CGeo g, int k, int f, const double *__restrict__ pa
   Ai[(lcp * nf + q) * ldA + int64_t(lin(g, oc)) * nf + f] = v;
 }
 
-constexpr int kPiece = 512;
+constexpr int kPiece = 1024;
 
 // rc = R v = P^T v, node by node.  The mesh nodes of each coarse cell are
 // stored together (cnodes) and cut into pieces; block p sums, for each of
@@ -310,8 +310,16 @@ __global__ void k_coarse_matvec(const T *__restrict__ Minv, int64_t ld, int64_t 
   const int64_t inst = r / nc0, lr = r % nc0;
   const T *row = Minv + inst * inst_stride + lr * ld;
   const T *x = rc + inst * nc0;
-  T s = T(0);
-  for (int64_t c = ln; c < nc0; c += 32) s = fma(row[c], x[c], s);
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);  // four chains for load parallelism
+  int64_t c = ln;
+  for (; c + 96 < nc0; c += 128) {
+    s0 = fma(row[c], x[c], s0);
+    s1 = fma(row[c + 32], x[c + 32], s1);
+    s2 = fma(row[c + 64], x[c + 64], s2);
+    s3 = fma(row[c + 96], x[c + 96], s3);
+  }
+  for (; c < nc0; c += 32) s0 = fma(row[c], x[c], s0);
+  T s = (s0 + s1) + (s2 + s3);
   s = warp_sum_t(s);
   if (ln == 0) zc[r] = s;
 }

@@ -59,6 +59,31 @@ __device__ __forceinline__ void block_sum_store(T (&v)[NV], T *out) {
   }
 }
 
+// Grid reductions without a second launch: every block stores its partials,
+// then the last block to finish (ticket counter, reset for the next launch)
+// sums each row over the blocks in block order -- in T within a lane and a
+// warp, one conversion to double per row.
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+template <typename T>
+__device__ __forceinline__ void sum_rows(const T *partial, int nrows, double *res) {
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  for (int k = wid; k < nrows; k += kB / 32) {
+    T s = T(0);
+    for (int b = ln; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (int64_t)k * gridDim.x + b);
+    s = warp_sum(s);
+    if (ln == 0) res[k] = double(s);
+  }
+}
+
 // res[k] = sum_b partial[k * nblocks + b] (double, fixed order), k < nv.
 // Skipped (res[k] = 0) when flag is given and *flag == 0.  Optional outputs
 // for a squared norm (nv == 1): scale = 1/sqrt(res) in P (0 if res <= 0) and
@@ -96,7 +121,8 @@ __global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int n
 template <typename T>
 __global__ void __launch_bounds__(kB) k_multidot(const T *__restrict__ V, int64_t ld, int nv,
                                                  const T *__restrict__ w, int64_t n, T *__restrict__ partial,
-                                                 const int *__restrict__ flag) {
+                                                 const int *__restrict__ flag, unsigned *__restrict__ counter,
+                                                 double *__restrict__ h) {
   if (flag && *flag == 0) return;
   constexpr int L = V16<T>::L, NV = 8;
   const int64_t nl = n / L;
@@ -126,14 +152,25 @@ __global__ void __launch_bounds__(kB) k_multidot(const T *__restrict__ V, int64_
     block_sum_store<T, NV>(acc, partial + (int64_t)i0 * gridDim.x);
     __syncthreads();  // the block-sum scratch is reused by the next group
   }
+  if (last_block(counter)) {
+    sum_rows<T>(partial, nv, h);
+    if (threadIdx.x == 0) *counter = 0;
+  }
 }
 
 // w -= sum_i h[i] V_i (i < nv) and block partial sums of the new |w|^2;
 // skipped when flag is given and *flag == 0.  Layout as k_multidot.
+// The last block writes |w|^2 to *nrm, the normalisation factor 1/|w| (0 if
+// |w| = 0) to *scale and, given `before` (|w|^2 before the projection), the
+// DGKS flag = (|w|^2 < 1e-4 before): the projection removed more than 99.99%
+// of |w|^2, so a second Gram-Schmidt pass is needed.
 template <typename T>
 __global__ void __launch_bounds__(kB) k_update_norm(const T *__restrict__ V, int64_t ld, int nv,
                                                     const double *__restrict__ h, T *__restrict__ w, int64_t n,
-                                                    const int *__restrict__ flag, T *__restrict__ partial) {
+                                                    const int *__restrict__ flag, T *__restrict__ partial,
+                                                    unsigned *__restrict__ counter, double *__restrict__ nrm,
+                                                    T *__restrict__ scale, const double *__restrict__ before,
+                                                    int *__restrict__ flag_out) {
   if (flag && *flag == 0) return;
   constexpr int L = V16<T>::L;
   __shared__ T hs[kMaxRestart + 1];
@@ -162,6 +199,18 @@ __global__ void __launch_bounds__(kB) k_update_norm(const T *__restrict__ V, int
     acc[0] = fma(s, s, acc[0]);
   }
   block_sum_store<T, 1>(acc, partial);
+  if (last_block(counter)) {
+    __shared__ double tot;
+    sum_rows<T>(partial, 1, &tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double t = tot;
+      *nrm = t;
+      *scale = t > 0.0 ? T(1.0 / sqrt(t)) : T(0);
+      if (flag_out) *flag_out = (t < 1e-4 * before[0]) ? 1 : 0;
+      *counter = 0;
+    }
+  }
 }
 
 // partial sums of x . y (double, any alignment)
@@ -313,16 +362,15 @@ int red_blocks() { return kRedBlocks; }
 
 template <typename T>
 void vec_multidot(const T *V, int64_t ld, int nv, const T *w, int64_t n, double *partial, double *h,
-                  cudaStream_t st, const int *flag) {
+                  cudaStream_t st, const int *flag, unsigned *counter) {
   T *pt = reinterpret_cast<T *>(partial);
-  k_multidot<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, w, n, pt, flag);
-  k_sum_partials<T><<<nv, kB, 0, st>>>(pt, kRedBlocks, nv, h, flag, nullptr, nullptr, nullptr);
-  note_launches(2);
+  k_multidot<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, w, n, pt, flag, counter, h);
+  note_launches(1);
 }
 template void vec_multidot<float>(const float *, int64_t, int, const float *, int64_t, double *, double *,
-                                  cudaStream_t, const int *);
+                                  cudaStream_t, const int *, unsigned *);
 template void vec_multidot<double>(const double *, int64_t, int, const double *, int64_t, double *, double *,
-                                   cudaStream_t, const int *);
+                                   cudaStream_t, const int *, unsigned *);
 
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st) {
   k_dot<<<kRedBlocks, kB, 0, st>>>(x, y, n, partial);
@@ -338,23 +386,23 @@ void vec_dot(const double *x, const double *y, int64_t n, double *partial, doubl
 // *scale = 1/|w| for vec_normalize.
 template <typename T>
 void vec_orthogonalize(T *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
-                       double *nrm, int *flag, T *scale, cudaStream_t st) {
+                       double *nrm, int *flag, T *scale, unsigned *counter, cudaStream_t st) {
   T *pt = reinterpret_cast<T *>(partial);
-  // pass 1 dots include w itself (stored right after V_{nv-1}): |w|^2
-  vec_multidot<T>(V, ld, nv + 1, V + (int64_t)nv * ld, n, partial, h1, st, nullptr);
   T *w = V + (int64_t)nv * ld;
-  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h1, w, n, nullptr, pt);
-  k_sum_partials<T><<<1, kB, 0, st>>>(pt, kRedBlocks, 1, nrm, nullptr, scale, h1 + nv, flag);
-  note_launches(2);
-  vec_multidot<T>(V, ld, nv, w, n, partial, h2, st, flag);
-  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h2, w, n, flag, pt);
-  k_sum_partials<T><<<1, kB, 0, st>>>(pt, kRedBlocks, 1, nrm + 1, flag, scale, nullptr, nullptr);
+  // pass 1 dots include w itself (stored right after V_{nv-1}): |w|^2 = h1[nv]
+  vec_multidot<T>(V, ld, nv + 1, w, n, partial, h1, st, nullptr, counter);
+  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h1, w, n, nullptr, pt, counter, nrm, scale, h1 + nv,
+                                              flag);
+  // pass 2, on the device flag
+  vec_multidot<T>(V, ld, nv, w, n, partial, h2, st, flag, counter);
+  k_update_norm<T><<<kRedBlocks, kB, 0, st>>>(V, ld, nv, h2, w, n, flag, pt, counter, nrm + 1, scale, nullptr,
+                                              nullptr);
   note_launches(2);
 }
 template void vec_orthogonalize<float>(float *, int64_t, int, int64_t, double *, double *, double *, double *,
-                                       int *, float *, cudaStream_t);
+                                       int *, float *, unsigned *, cudaStream_t);
 template void vec_orthogonalize<double>(double *, int64_t, int, int64_t, double *, double *, double *, double *,
-                                        int *, double *, cudaStream_t);
+                                        int *, double *, unsigned *, cudaStream_t);
 
 template <typename T>
 void vec_normalize(T *w, int64_t n, const T *scale, cudaStream_t st) {

@@ -17,15 +17,16 @@ constexpr int64_t kVecAlign = 64;
 inline int64_t vec_ld(int64_t n) { return (n + kVecAlign - 1) / kVecAlign * kVecAlign; }
 
 // h[i] = V_i . w for i < nv; partial: (nv + 8) * red_blocks() doubles;
-// skipped (h = 0) when flag is given and *flag == 0
+// counter: a device word that is zero between launches (grid reduction
+// ticket); skipped (h unchanged) when flag is given and *flag == 0
 template <typename T>
 void vec_multidot(const T *V, int64_t ld, int nv, const T *w, int64_t n, double *partial, double *h,
-                  cudaStream_t st, const int *flag = nullptr);
+                  cudaStream_t st, const int *flag, unsigned *counter);
 // x . y (double)
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st);
 template <typename T>
 void vec_orthogonalize(T *V, int64_t ld, int nv, int64_t n, double *partial, double *h1, double *h2,
-                       double *nrm, int *flag, T *scale, cudaStream_t st);
+                       double *nrm, int *flag, T *scale, unsigned *counter, cudaStream_t st);
 template <typename T>
 void vec_normalize(T *w, int64_t n, const T *scale, cudaStream_t st);
 // r = b - y
