@@ -100,6 +100,8 @@ struct Coarse {
   int32_t *piece_cell = nullptr;    // n_pieces
   int32_t *piece_begin = nullptr;   // n_pieces + 1: ranges in cnodes
   int32_t *cell_piece = nullptr;    // ncell + 1: pieces of each cell
+  int32_t *sptr = nullptr;          // ncn + 1: restriction-sum entries of each coarse node
+  int32_t *sent = nullptr;          // entries piece * 2^dim + corner
   DevBuf M;                         // per instance [A_c | I] -> [I | A_c^{-1}], nc0 x 2nc0 doubles
   DevBuf Minv32;                    // per instance A_c^{-1} rounded to float, nc0 x nc0
   DevBuf vec;                       // coarse work vectors and operator-build partials

@@ -263,40 +263,21 @@ __global__ void __launch_bounds__(kB) k_restrict_cells(CGeo g, const float *__re
   }
 }
 
-// rc[c', q]: the corner sums of the cells around coarse node c' (each cell's
-// pieces in order), one warp per coarse unknown, double sums
-template <typename T, int DIM>
-__global__ void k_restrict_sum(CGeo g, int64_t ncn, const int32_t *__restrict__ cell_piece,
-                               const T *__restrict__ part, T *__restrict__ rc) {
-  constexpr int NC = 1 << DIM;
+// rc[c', q]: the corner sums of the cells around coarse node c' -- the
+// (piece, corner) entries listed for c' (corner by corner, each cell's
+// pieces in order) -- one warp per coarse unknown, lanes over the entries
+template <typename T>
+__global__ void k_restrict_sum(int64_t nc, int nf, const int32_t *__restrict__ sptr,
+                               const int32_t *__restrict__ sent, const T *__restrict__ part, T *__restrict__ rc) {
   const int64_t t = (blockIdx.x * int64_t(kB) + threadIdx.x) >> 5;
   const int ln = threadIdx.x & 31;
-  const int nf = g.nf;
-  if (t >= ncn * nf) return;
-  const int64_t cp = t / nf, inst = cp / g.ncn_inst;
+  if (t >= nc) return;
+  const int64_t cp = t / nf;
   const int q = int(t % nf);
-  int cc[3] = {0, 0, 0};
-  {
-    int r = int(cp % g.ncn_inst);
-    for (int a = 0; a < DIM; ++a) { cc[a] = r % g.nc1; r /= g.nc1; }
-  }
-  double sum = 0.0;
-#pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    int cell = 0;
-    bool ok = true;
-    for (int a = DIM - 1; a >= 0; --a) {
-      const int ca = cc[a] - ((s >> a) & 1);
-      if (ca < 0 || ca > g.nc1 - 2) ok = false;
-      cell = cell * (g.nc1 - 1) + ca;
-    }
-    if (!ok) continue;
-    const int64_t gc = inst * g.ncell_inst + cell;
-    for (int p = cell_piece[gc] + ln; p < cell_piece[gc + 1]; p += 32)
-      sum += double(part[(int64_t(p) * NC + s) * nf + q]);
-  }
-  sum = warp_sum(sum);
-  if (ln == 0) rc[t] = T(sum);
+  T sum = T(0);
+  for (int e = sptr[cp] + ln; e < sptr[cp + 1]; e += 32) sum += part[int64_t(sent[e]) * nf + q];
+  sum = warp_sum_t(sum);
+  if (ln == 0) rc[t] = sum;
 }
 
 // zc = A_c^{-1} rc, one warp per row, in precision T; row r of instance i at
@@ -468,6 +449,9 @@ void Coarse::release() {
   cudaFree(piece_cell);
   cudaFree(piece_begin);
   cudaFree(cell_piece);
+  cudaFree(sptr);
+  cudaFree(sent);
+  sptr = sent = nullptr;
   pos = nullptr;
   rstart = nullptr;
   rnode = nullptr;
@@ -570,6 +554,30 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   }
   cell_piece[ncell] = (int32_t)piece_cell.size();
   piece_begin.push_back((int32_t)m->n_nodes);
+  // restriction-sum lists: for coarse node c', entries piece * 2^dim + corner
+  // of the cells around it (corner of c' in that cell), corner by corner
+  std::vector<int32_t> sptr(ncn_all + 1, 0), sent;
+  for (int64_t cp = 0; cp < ncn_all; ++cp) {
+    const int64_t inst = cp / ncn;
+    int cc[3] = {0, 0, 0};
+    {
+      int64_t r = cp % ncn;
+      for (int a = 0; a < dim; ++a) { cc[a] = int(r % nc1); r /= nc1; }
+    }
+    for (int s = 0; s < (1 << dim); ++s) {
+      int64_t cell = 0;
+      bool ok = true;
+      for (int a = dim - 1; a >= 0; --a) {
+        const int ca = cc[a] - ((s >> a) & 1);
+        if (ca < 0 || ca > nc1 - 2) ok = false;
+        cell = cell * (nc1 - 1) + ca;
+      }
+      if (!ok) continue;
+      const int64_t gc = inst * ncell_inst + cell;
+      for (int32_t p = cell_piece[gc]; p < cell_piece[gc + 1]; ++p) sent.push_back(p * (1 << dim) + s);
+    }
+    sptr[cp + 1] = (int32_t)sent.size();
+  }
   const int64_t np = (int64_t)piece_cell.size();
   CHNS_CUDA_TRY(cudaMalloc(&C.cnodes, sizeof(int32_t) * std::max<size_t>(cnodes.size(), 1)));
   CHNS_CUDA_TRY(cudaMemcpy(C.cnodes, cnodes.data(), sizeof(int32_t) * cnodes.size(), cudaMemcpyHostToDevice));
@@ -577,6 +585,10 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   CHNS_CUDA_TRY(cudaMemcpy(C.piece_cell, piece_cell.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice));
   CHNS_CUDA_TRY(cudaMalloc(&C.piece_begin, sizeof(int32_t) * (np + 1)));
   CHNS_CUDA_TRY(cudaMemcpy(C.piece_begin, piece_begin.data(), sizeof(int32_t) * (np + 1), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.sptr, sizeof(int32_t) * sptr.size()));
+  CHNS_CUDA_TRY(cudaMemcpy(C.sptr, sptr.data(), sizeof(int32_t) * sptr.size(), cudaMemcpyHostToDevice));
+  CHNS_CUDA_TRY(cudaMalloc(&C.sent, sizeof(int32_t) * std::max<size_t>(sent.size(), 1)));
+  CHNS_CUDA_TRY(cudaMemcpy(C.sent, sent.data(), sizeof(int32_t) * sent.size(), cudaMemcpyHostToDevice));
   CHNS_CUDA_TRY(cudaMalloc(&C.cell_piece, sizeof(int32_t) * (ncell + 1)));
   CHNS_CUDA_TRY(cudaMemcpy(C.cell_piece, cell_piece.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice));
   C.ncell_inst = ncell_inst;
@@ -659,13 +671,11 @@ void precond_apply(chns_mesh *m, const T *Binv, bool coarse, const T *v, T *z, c
     T *part = reinterpret_cast<T *>(C.rpart.as<double>());
     const unsigned np = (unsigned)C.n_pieces;
     const unsigned gs = (unsigned)((C.nc * 32 + kB - 1) / kB);
-    if (m->dim == 2) {
+    if (m->dim == 2)
       k_restrict_cells<T, 5, 2><<<np, kB, 0, st>>>(g, C.pos, C.cnodes, C.piece_cell, C.piece_begin, v, part);
-      k_restrict_sum<T, 2><<<gs, kB, 0, st>>>(g, C.ncn, C.cell_piece, part, rc);
-    } else {
+    else
       k_restrict_cells<T, 6, 3><<<np, kB, 0, st>>>(g, C.pos, C.cnodes, C.piece_cell, C.piece_begin, v, part);
-      k_restrict_sum<T, 3><<<gs, kB, 0, st>>>(g, C.ncn, C.cell_piece, part, rc);
-    }
+    k_restrict_sum<T><<<gs, kB, 0, st>>>(C.nc, m->nf, C.sptr, C.sent, part, rc);
     const unsigned gm = (unsigned)((C.nc * 32 + kB - 1) / kB);
     if (sizeof(T) == sizeof(float))
       k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.Minv32.as<float>()), C.nc0,

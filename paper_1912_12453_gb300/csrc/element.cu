@@ -554,28 +554,37 @@ __global__ void k_cast(const double *__restrict__ x, int64_t n, T *__restrict__ 
 }
 
 // y[i] = sum over the slots of node i of weight * E[slot] (fixed order), then
-// the constrained rows: y = w on wall velocities and the pinned pressure
+// the constrained rows: y = w on wall velocities and the pinned pressure.
+// The slots of a node are fetched eight at a time (independent loads), then
+// added in list order.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_gather_nodes(const int32_t *__restrict__ gptr,
                                                       const int32_t *__restrict__ gent,
                                                       const uint8_t *__restrict__ nflag, int64_t n_nodes,
                                                       const T *__restrict__ E, const T *__restrict__ w,
                                                       T *__restrict__ y) {
-  constexpr int NF = D + 3;
+  constexpr int NF = D + 3, G = 8;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_nodes; i += int64_t(gridDim.x) * blockDim.x) {
     T acc[NF];
 #pragma unroll
     for (int k = 0; k < NF; ++k) acc[k] = T(0);
-    const int p1 = gptr[i + 1];
-    for (int p = gptr[i]; p < p1; ++p) {
-      const uint32_t ent = uint32_t(gent[p]);
-      const int64_t slot = int64_t(ent & 0x3fffffffu);
-      const uint32_t code = ent >> 30;
-      const T wt = code == 0 ? T(1) : (code == 1 ? T(0.5) : T(0.25));
-      T v[NF];
-      load_block<NF>(E + slot * NF, v);
+    const int p0 = gptr[i], p1 = gptr[i + 1];
+    for (int pb = p0; pb < p1; pb += G) {
+      uint32_t ent[G];
 #pragma unroll
-      for (int k = 0; k < NF; ++k) acc[k] = fma(wt, v[k], acc[k]);
+      for (int g = 0; g < G; ++g) ent[g] = pb + g < p1 ? uint32_t(gent[pb + g]) : 0xffffffffu;
+      T v[G][NF];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (ent[g] != 0xffffffffu) load_block<NF>(E + int64_t(ent[g] & 0x3fffffffu) * NF, v[g]);
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (ent[g] != 0xffffffffu) {
+          const uint32_t code = ent[g] >> 30;
+          const T wt = code == 0 ? T(1) : (code == 1 ? T(0.5) : T(0.25));
+#pragma unroll
+          for (int k = 0; k < NF; ++k) acc[k] = fma(wt, v[g][k], acc[k]);
+        }
     }
     const uint8_t fl = nflag[i];
     if (fl & 1)
