@@ -38,14 +38,16 @@ from paper_1912_12453_gb300 import workloads as W  # noqa: E402
 METRIC = "Jacobian-apply GDoF/s and s per CN step, FP32-mixed vs FP64 at equal residual"
 WORKLOAD = "droplet3d_l6"
 # FP32 operations per element of one 3D J.w apply, counted by ncu on the
-# element kernel (thread-level FADD + FMUL + 2 x FFMA, 3.547e8 per launch of
-# 32,768 elements; profiles/jacvec_fp32_droplet3d_l6.md).
+# element kernel (thread-level FADD + FMUL + 2 x FFMA: 3.547e8 per 32,768
+# elements; profiles/jacvec_fp32_droplet3d_l6.md).
 JV_FLOP_PER_ELEM_3D = 10825
-# DRAM bytes of one J.w apply (8 colour launches) of the level-6 droplet mesh,
-# read + write, from one ncu capture with --cache-control none after an L2
-# flush (same file).  Valid for the kernel as profiled; null for other meshes.
-JV_TRAFFIC_PER_APPLY = {262144: 15_311_872 + 37_344_768}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# DRAM bytes of one J.w apply (element kernel + node gather) of the level-6
+# droplet mesh, read + write, from one ncu capture with --cache-control none
+# (same file).  Valid for the kernels as profiled; null for other meshes.
+JV_TRAFFIC_PER_APPLY = {262144: 45_309_312 + 90_735_360}
+# FP32 FMA-pipe peak measured on GB300 by probes/fma_peak.cu
+# (profiles/fma_peaks_gb300.md); the derived 152 x 128 x 2 x 2.07 GHz is 80.5.
+FP32_PEAK_TFLOPS = 78.37
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -357,10 +359,10 @@ def main():
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS,
                 "traffic": JV_TRAFFIC_PER_APPLY.get(mesh.n_elem) if mesh.dim == 3 else None,
-                "per": f"one J.w apply ({mesh.n_colours} colour launches, {mesh.n_elem} elements, "
+                "per": f"one J.w apply (element kernel over {mesh.n_elem} leaves + node gather, "
                        f"{JV_FLOP_PER_ELEM_3D} flop/element)",
-                "kernel": "k_element<3,float,J.w>",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "kernel": "k_element<3,float,J.w> + k_gather_nodes<3,float>",
+                "peak_source": "measured FP32 FMA pipe (probes/fma_peak.cu)",
                 "hbm_gbs_achieved": (JV_TRAFFIC_PER_APPLY.get(mesh.n_elem, 0) / (jv_apply_ms / 1e3) / 1e9)
                 if mesh.dim == 3 else None}
 
@@ -412,7 +414,7 @@ def main():
                     "d2h_bytes_per_step": n_dof * 8},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
-            "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "fp32_tflops_derived": FP32_PEAK_TFLOPS},
+            "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "fp32_fma_tflops_measured": FP32_PEAK_TFLOPS},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
