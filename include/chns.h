@@ -84,7 +84,7 @@ typedef struct {
                               Newton iteration */
   int coarse_level;        /* two-level preconditioner: coarse octree level L_c >= 1 (at most one
                               below the coarsest leaf); 0 = block-Jacobi only; -1 = automatic
-                              (L_c = min(2, coarsest leaf level - 1), off if that is < 1) */
+                              (L_c = min(3, coarsest leaf level - 1), off if that is < 1) */
 } chns_solver_opts;
 
 typedef struct {

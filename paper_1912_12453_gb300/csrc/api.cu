@@ -504,7 +504,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   const bool mixed = o.precision == CHNS_FP32_BULK;
   bool use64 = !mixed;
   int Lc = o.coarse_level;
-  if (Lc < 0) Lc = std::min(2, m->min_level - 1);
+  if (Lc < 0) Lc = std::min(3, m->min_level - 1);
   const bool coarse = Lc >= 1;
   if (coarse) TRY(coarse_setup(m, Lc));
   // a preconditioner from an earlier step is reused while it is young enough

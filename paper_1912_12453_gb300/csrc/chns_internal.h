@@ -102,8 +102,9 @@ struct Coarse {
   int32_t *cell_piece = nullptr;    // ncell + 1: pieces of each cell
   int32_t *sptr = nullptr;          // ncn + 1: restriction-sum entries of each coarse node
   int32_t *sent = nullptr;          // entries piece * 2^dim + corner
-  DevBuf M;                         // per instance [A_c | I] -> [I | A_c^{-1}], nc0 x 2nc0 doubles
-  DevBuf Minv32;                    // per instance A_c^{-1} rounded to float, nc0 x nc0
+  DevBuf M;                         // per instance A_c -> A_c^{-1} (double), nc0 x nc0
+  DevBuf Minv32;                    // per instance A_c^{-1} in float, nc0 x nc0
+  DevBuf piv;                       // Gauss-Jordan row interchanges, nc0 per instance
   DevBuf vec;                       // coarse work vectors and operator-build partials
   DevBuf rpart;                     // restriction partials, n_pieces x 2^dim x nf doubles
   bool ready = false;

@@ -123,6 +123,7 @@ constexpr int kChunks = 16;
 // Block (c', sl) takes the sl-th of kChunks slices of the restriction list of
 // coarse row node c' and, for the probed colour k, sums P[i, c'] y[i, q] per
 // owner slot (the owner of mesh node i: the nearest coarse node of colour k).
+// Sums in T within the block (fixed order), one partial per slice.
 template <typename T, int NF>
 __global__ void __launch_bounds__(kB) k_gather_coarse(CGeo g, const int64_t *__restrict__ rstart,
                                                       const int32_t *__restrict__ rnode,
@@ -134,16 +135,16 @@ __global__ void __launch_bounds__(kB) k_gather_coarse(CGeo g, const int64_t *__r
     int r = int(cp % g.ncn_inst);
     for (int a = 0; a < g.dim; ++a) { cpc[a] = r % g.nc1; r /= g.nc1; }
   }
-  double acc[8][NF];
+  T acc[8][NF];
 #pragma unroll
   for (int s = 0; s < 8; ++s)
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[s][q] = 0.0;
+    for (int q = 0; q < NF; ++q) acc[s][q] = T(0);
   const int64_t b0 = rstart[cp], len = rstart[cp + 1] - b0;
   const int64_t lo = b0 + len * sl / kChunks, hi = b0 + len * (sl + 1) / kChunks;
   for (int64_t e = lo + threadIdx.x; e < hi; e += kB) {
     const int64_t i = rnode[e];
-    const double wgt = rw[e];
+    const T wgt = T(rw[e]);
     int slot = 0;
     bool ok = true;
     for (int a = 0; a < g.dim; ++a) {
@@ -153,30 +154,30 @@ __global__ void __launch_bounds__(kB) k_gather_coarse(CGeo g, const int64_t *__r
       if (o > cpc[a]) slot |= 1 << a;
     }
     if (!ok) continue;
-    double yq[NF];
+    T yq[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) yq[q] = double(y[i * NF + q]);
+    for (int q = 0; q < NF; ++q) yq[q] = y[i * NF + q];
 #pragma unroll
     for (int s = 0; s < 8; ++s)
       if (s == slot)
 #pragma unroll
-        for (int q = 0; q < NF; ++q) acc[s][q] += wgt * yq[q];
+        for (int q = 0; q < NF; ++q) acc[s][q] = fma(wgt, yq[q], acc[s][q]);
   }
-  __shared__ double red[kB / 32][NF];
+  __shared__ T red[kB / 32][8 * NF];
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < 8; ++s)
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
-      double v = warp_sum(acc[s][q]);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+      const T v = warp_sum_t(acc[s][q]);
+      if (ln == 0) red[wid][s * NF + q] = v;
     }
-    __syncthreads();
-    if (threadIdx.x < NF) {
-      double v = 0.0;
-      for (int w = 0; w < kB / 32; ++w) v += red[w][threadIdx.x];
-      part[((int64_t(cp) * kChunks + sl) * 8 + s) * NF + threadIdx.x] = v;
-    }
-    __syncthreads();
+  __syncthreads();
+  for (int t = threadIdx.x; t < 8 * NF; t += kB) {
+    T v = T(0);
+#pragma unroll
+    for (int w = 0; w < kB / 32; ++w) v += red[w][t];
+    part[(int64_t(cp) * kChunks + sl) * 8 * NF + t] = double(v);
   }
 }
 
@@ -361,37 +362,31 @@ __global__ void __launch_bounds__(kB) k_block_prolong(CGeo g, const float *__res
   }
 }
 
-// A_c^{-1} of every instance rounded to T, compact (nc0 x nc0 each)
+// A -> B elementwise with a type change (n values)
+template <typename A, typename B>
+__global__ void k_copy_cast(const A *__restrict__ x, int64_t n, B *__restrict__ y) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB) y[t] = B(x[t]);
+}
+
+// In-place Gauss-Jordan inversion of each instance's n x n block (row-major)
+// with partial pivoting: pivot step k swaps the row of the largest |a_rk|,
+// r >= k, into row k (recorded in piv), scales row k by d = 1/a_kk and puts
+// d on the diagonal, and eliminates column k from the other rows, whose
+// column k becomes -a_rk d; the recorded row interchanges are undone as
+// column interchanges at the end.  No [A | I] copy: the working set is n^2
+// values (76.5 MB in float at n = 4374, inside L2).
 template <typename T>
-__global__ void k_extract_inverse(const double *__restrict__ M, int64_t nc0, int n_inst, T *__restrict__ out) {
-  const int64_t per = nc0 * nc0;
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < per * n_inst; t += int64_t(gridDim.x) * kB) {
-    const int64_t inst = t / per, r = (t % per) / nc0, c = t % nc0;
-    out[t] = T(M[inst * nc0 * 2 * nc0 + r * 2 * nc0 + nc0 + c]);
-  }
-}
-
-// [A | I] setup for every instance block (nc0 x 2 nc0 each)
-__global__ void k_gj_init(double *__restrict__ M, int64_t nc0, int n_inst) {
-  const int64_t per = nc0 * nc0;
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < per * n_inst; t += int64_t(gridDim.x) * kB) {
-    const int64_t inst = t / per, r = (t % per) / nc0, c = t % nc0;
-    M[inst * nc0 * 2 * nc0 + r * 2 * nc0 + nc0 + c] = r == c ? 1.0 : 0.0;
-  }
-}
-
-// pivot step k of instance blockIdx.x: pick the largest |M[r][k]|, r >= k,
-// swap it into row k, scale row k, save column k for the elimination
-__global__ void k_gj_pivot(double *__restrict__ Mall, int64_t nc, int64_t k, double *__restrict__ colall,
-                           int *__restrict__ bad) {
-  double *M = Mall + int64_t(blockIdx.x) * nc * 2 * nc;
-  double *col = colall + int64_t(blockIdx.x) * nc;
-  __shared__ double bv[1024];
+__global__ void k_gj_pivot(T *__restrict__ Mall, int64_t n, int64_t k, T *__restrict__ colall,
+                           int32_t *__restrict__ pivall, int *__restrict__ bad) {
+  T *M = Mall + int64_t(blockIdx.x) * n * n;
+  T *col = colall + int64_t(blockIdx.x) * n;
+  __shared__ T bv[1024];
   __shared__ int64_t bi[1024];
-  double best = -1.0;
+  __shared__ T pv;
+  T best = T(-1);
   int64_t arg = k;
-  for (int64_t r = k + threadIdx.x; r < nc; r += blockDim.x) {
-    double v = fabs(M[r * 2 * nc + k]);
+  for (int64_t r = k + threadIdx.x; r < n; r += blockDim.x) {
+    const T v = fabs(M[r * n + k]);
     if (v > best) { best = v; arg = r; }
   }
   bv[threadIdx.x] = best;
@@ -408,31 +403,75 @@ __global__ void k_gj_pivot(double *__restrict__ Mall, int64_t nc, int64_t k, dou
     __syncthreads();
   }
   const int64_t p = bi[0];
-  const double piv = M[p * 2 * nc + k];
-  if (!(fabs(piv) > 0.0)) {
-    if (threadIdx.x == 0) *bad = 1;
-    for (int64_t r = threadIdx.x; r < nc; r += blockDim.x) col[r] = 0.0;
-    return;
-  }
-  for (int64_t j = threadIdx.x; j < 2 * nc; j += blockDim.x) {
-    double a = M[k * 2 * nc + j], b = M[p * 2 * nc + j];
-    if (p != k) M[p * 2 * nc + j] = a;
-    M[k * 2 * nc + j] = b / piv;
+  if (threadIdx.x == 0) {
+    pv = M[p * n + k];
+    pivall[int64_t(blockIdx.x) * n + k] = int32_t(p);
   }
   __syncthreads();
-  for (int64_t r = threadIdx.x; r < nc; r += blockDim.x) col[r] = r == k ? 0.0 : M[r * 2 * nc + k];
+  if (!(fabs(pv) > T(0))) {
+    if (threadIdx.x == 0) *bad = 1;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) col[r] = T(0);
+    return;
+  }
+  const T d = T(1) / pv;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const T a = M[k * n + j], b = M[p * n + j];
+    if (p != k) M[p * n + j] = a;
+    M[k * n + j] = j == k ? d : b * d;
+  }
+  __syncthreads();
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) col[r] = r == k ? T(0) : M[r * n + k];
 }
 
-// eliminate column k from every row but k (instance blockIdx.y)
-__global__ void k_gj_elim(double *__restrict__ Mall, int64_t nc, int64_t k, const double *__restrict__ colall) {
-  double *M = Mall + int64_t(blockIdx.y) * nc * 2 * nc;
-  const double *col = colall + int64_t(blockIdx.y) * nc;
-  const int64_t W = 2 * nc;
-  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < nc * W; t += int64_t(gridDim.x) * kB) {
-    const int64_t r = t / W, j = t % W;
-    const double fr = col[r];
-    if (fr != 0.0) M[t] -= fr * M[k * W + j];
+// elimination of column k: thread = one column j (coalesced along rows of
+// the row-major block), block y = a range of kRowsGJ rows, z = instance
+constexpr int kRowsGJ = 32;
+template <typename T>
+__global__ void __launch_bounds__(kB) k_gj_elim(T *__restrict__ Mall, int64_t n, int64_t k,
+                                                const T *__restrict__ colall) {
+  T *M = Mall + int64_t(blockIdx.z) * n * n;
+  const T *col = colall + int64_t(blockIdx.z) * n;
+  const int64_t j = blockIdx.x * int64_t(kB) + threadIdx.x;
+  if (j >= n) return;
+  const T d = M[k * n + k];
+  const T rk = M[k * n + j];
+  const int64_t r0 = int64_t(blockIdx.y) * kRowsGJ, r1 = r0 + kRowsGJ < n ? r0 + kRowsGJ : n;
+  for (int64_t r = r0; r < r1; ++r) {
+    if (r == k) continue;
+    const T fr = col[r];
+    T *a = M + r * n + j;
+    if (j == k) *a = -fr * d;
+    else if (fr != T(0)) *a = fma(-fr, rk, *a);
   }
+}
+
+// undo the row interchanges as column interchanges, last first (a thread per row)
+template <typename T>
+__global__ void k_gj_unswap(T *__restrict__ Mall, int64_t n, const int32_t *__restrict__ pivall, int n_inst) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n * n_inst; t += int64_t(gridDim.x) * kB) {
+    const int64_t inst = t / n, r = t % n;
+    T *row = Mall + inst * n * n + r * n;
+    const int32_t *piv = pivall + inst * n;
+    for (int64_t k = n - 1; k >= 0; --k) {
+      const int64_t p = piv[k];
+      if (p != k) {
+        const T x = row[k];
+        row[k] = row[p];
+        row[p] = x;
+      }
+    }
+  }
+}
+
+template <typename T>
+void gauss_jordan(T *M, int64_t n, int n_inst, T *col, int32_t *piv, int *bad, cudaStream_t st) {
+  const dim3 ge((unsigned)((n + kB - 1) / kB), (unsigned)((n + kRowsGJ - 1) / kRowsGJ), (unsigned)n_inst);
+  for (int64_t k = 0; k < n; ++k) {
+    k_gj_pivot<T><<<n_inst, 1024, 0, st>>>(M, n, k, col, piv, bad);
+    k_gj_elim<T><<<ge, kB, 0, st>>>(M, n, k, col);
+  }
+  k_gj_unswap<T><<<grid_n(n * n_inst), kB, 0, st>>>(M, n, piv, n_inst);
+  note_launches(int(2 * n + 1));
 }
 
 }  // namespace
@@ -460,6 +499,7 @@ void Coarse::release() {
   ncell_inst = ncell = n_pieces = 0;
   M.release();
   Minv32.release();
+  piv.release();
   vec.release();
   rpart.release();
   level = -1;
@@ -601,7 +641,8 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   C.nc0 = ncn * nf;
   C.ncn = ncn_all;
   C.nc = ncn_all * nf;
-  TRY_CHNS(C.M.ensure(sizeof(double) * C.nc0 * 2 * C.nc0 * ni));
+  TRY_CHNS(C.M.ensure(sizeof(double) * C.nc0 * C.nc0 * ni));
+  TRY_CHNS(C.piv.ensure(sizeof(int32_t) * C.nc0 * ni));
   TRY_CHNS(C.Minv32.ensure(sizeof(float) * C.nc0 * C.nc0 * ni));
   TRY_CHNS(C.vec.ensure(sizeof(double) * (3 * C.nc + 8 + C.ncn * kChunks * 8 * nf)));
   TRY_CHNS(C.rpart.ensure(sizeof(double) * std::max<int64_t>(np, 1) * (1 << dim) * nf));
@@ -614,8 +655,8 @@ chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaSt
   const int nf = m->nf, dim = m->dim;
   CGeo g{dim, nf, C.nc1, m->n_nodes, C.ncn_inst, C.nc0, C.ncell_inst};
   double *M = C.M.as<double>();
-  const int64_t nc0 = C.nc0;
-  CHNS_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nc0 * 2 * nc0 * C.n_inst, st));
+  const int64_t nc0 = C.nc0, nn = nc0 * nc0 * C.n_inst;
+  CHNS_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nn, st));
   const int ncol = dim == 2 ? 9 : 27;
   double *part = C.vec.as<double>() + 3 * C.nc + 8;
   for (int k = 0; k < ncol; ++k)
@@ -629,27 +670,32 @@ chns_status coarse_build(chns_mesh *m, JvFn<T> jv, void *ctx, T *w, T *y, cudaSt
         k_gather_coarse<T, 5><<<gr, kB, 0, st>>>(g, C.rstart, C.rnode, C.rw, C.pos, k, y, part);
       else
         k_gather_coarse<T, 6><<<gr, kB, 0, st>>>(g, C.rstart, C.rnode, C.rw, C.pos, k, y, part);
-      k_gather_sum<<<(unsigned)((C.ncn * 8 * nf + kB - 1) / kB), kB, 0, st>>>(g, k, f, part, M, 2 * nc0, C.ncn);
+      k_gather_sum<<<(unsigned)((C.ncn * 8 * nf + kB - 1) / kB), kB, 0, st>>>(g, k, f, part, M, nc0, C.ncn);
       note_launches(2);
     }
-  // Gauss-Jordan with partial pivoting on each instance's [A | I]
-  double *col = C.vec.as<double>() + 2 * C.nc;  // nc0 per instance = C.nc in total
+  // A_c^{-1} per instance, in the element precision: the FP32 path inverts
+  // in float (A_c is ill-conditioned along a pressure direction only, which
+  // float resolves: per-field errors of the applied inverse ~1e-6 at
+  // cond(A_c) ~ 1e9), the FP64 path in double.  Both copies are kept: M in
+  // double, Minv32 in float.
+  void *colv = C.vec.as<double>() + 2 * C.nc;  // nc0 per instance
   int *bad = reinterpret_cast<int *>(C.vec.as<double>() + 3 * C.nc);
+  int32_t *piv = C.piv.as<int32_t>();
+  float *M32 = C.Minv32.as<float>();
   CHNS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  k_gj_init<<<grid_n(nc0 * nc0 * C.n_inst), kB, 0, st>>>(M, nc0, C.n_inst);
-  note_launches(1);
-  const unsigned gx = std::max(1u, grid_n(nc0 * 2 * nc0) / (unsigned)std::max(1, std::min(C.n_inst, 8)));
-  for (int64_t k = 0; k < nc0; ++k) {
-    k_gj_pivot<<<C.n_inst, 1024, 0, st>>>(M, nc0, k, col, bad);
-    k_gj_elim<<<dim3(gx, C.n_inst), kB, 0, st>>>(M, nc0, k, col);
-    note_launches(2);
+  if (sizeof(T) == sizeof(float)) {
+    k_copy_cast<double, float><<<grid_n(nn), kB, 0, st>>>(M, nn, M32);
+    gauss_jordan<float>(M32, nc0, C.n_inst, static_cast<float *>(colv), piv, bad, st);
+    k_copy_cast<float, double><<<grid_n(nn), kB, 0, st>>>(M32, nn, M);
+  } else {
+    gauss_jordan<double>(M, nc0, C.n_inst, static_cast<double *>(colv), piv, bad, st);
+    k_copy_cast<double, float><<<grid_n(nn), kB, 0, st>>>(M, nn, M32);
   }
+  note_launches(2);
   int hbad = 0;
   CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   CHNS_CUDA_TRY(cudaStreamSynchronize(st));
   if (hbad) { set_error("singular coarse operator"); return CHNS_ERR_KRYLOV; }
-  k_extract_inverse<float><<<grid_n(nc0 * nc0 * C.n_inst), kB, 0, st>>>(M, nc0, C.n_inst, C.Minv32.as<float>());
-  note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error("coarse build: %s", cudaGetErrorString(e)); return CHNS_ERR_CUDA; }
   C.ready = true;
@@ -681,8 +727,8 @@ void precond_apply(chns_mesh *m, const T *Binv, bool coarse, const T *v, T *z, c
       k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.Minv32.as<float>()), C.nc0,
                                             C.nc0 * C.nc0, C.nc, C.nc0, rc, zc);
     else
-      k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.M.as<double>() + C.nc0), 2 * C.nc0,
-                                            2 * C.nc0 * C.nc0, C.nc, C.nc0, rc, zc);
+      k_coarse_matvec<T><<<gm, kB, 0, st>>>(reinterpret_cast<const T *>(C.M.as<double>()), C.nc0,
+                                            C.nc0 * C.nc0, C.nc, C.nc0, rc, zc);
     note_launches(3);
   }
   const int32_t *ni = (use && m->n_inst > 1) ? m->node_inst : nullptr;
