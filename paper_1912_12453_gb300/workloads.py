@@ -341,7 +341,7 @@ def batched_workloads(n: int = 64, seed: int = 7) -> List[Workload]:
     for i in range(n):
         dim = 2 if rng.random() < 0.5 else 3
         top = int(rng.integers(6, 10)) if dim == 2 else int(rng.integers(5, 8))
-        base = max(2, top - 3)
+        base = top - 2  # coarsest leaves at level >= 3: the coarse space of a union is level >= 2
         R = float(rng.uniform(0.1, 0.25))
         rho_r = float(10 ** rng.uniform(-3, 0))
         eta_r = float(10 ** rng.uniform(-2, 0))
