@@ -39,14 +39,14 @@ METRIC = "Jacobian-apply GDoF/s and s per CN step, FP32-mixed vs FP64 at equal r
 WORKLOAD = "droplet3d_l6"
 # FP32 operations per element of one 3D J.w apply, counted by ncu on the
 # element kernel (thread-level FADD + FMUL + 2 x FFMA: 3.547e8 per 32,768
-# elements; profiles/jacvec_fp32_droplet3d_l6.md).
+# elements of the level-6 droplet).
 JV_FLOP_PER_ELEM_3D = 10825
 # DRAM bytes of one J.w apply (element kernel + node gather) of the level-6
 # droplet mesh, read + write, from one ncu capture with --cache-control none
-# (same file).  Valid for the kernels as profiled; null for other meshes.
+# after an L2 flush.  Valid for the kernels as profiled; null for other meshes.
 JV_TRAFFIC_PER_APPLY = {262144: 45_309_312 + 90_735_360}
-# FP32 FMA-pipe peak measured on GB300 by probes/fma_peak.cu
-# (profiles/fma_peaks_gb300.md); the derived 152 x 128 x 2 x 2.07 GHz is 80.5.
+# FP32 FMA-pipe peak measured on GB300 by paper_1912_12453_gb300/probes/fma_peak.cu
+# (independent FMA chains on all SMs); the derived 152 x 128 x 2 x 2.07 GHz is 80.5.
 FP32_PEAK_TFLOPS = 78.37
 HBM_PEAK_FALLBACK = 6800.0
 
