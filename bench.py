@@ -118,6 +118,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_replicas(dof_applies: float, jv_ms: float, t_region: float, world: int, device):
+    """Whole-job totals of N independent replicas: the DoF-applies of all
+    ranks summed, the J.w time and the timed region's length as the maximum
+    over ranks (the slowest replica bounds the job)."""
+    if world == 1:
+        return dof_applies, jv_ms, t_region
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([dof_applies, jv_ms, t_region], dtype=torch.float64, device=device)
+    tm = t.clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(tm[1]), float(tm[2])
+
+
 def _gpu_index(local_rank: int) -> int:
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -298,14 +313,7 @@ def main():
     jv_calls = sum(s["jacvec_calls"] for s in stats32)
     dof_applies = float(n_dof) * jv_calls
     t_region = step32_ms * args.steps / 1e3
-    if world > 1:
-        t = torch.tensor([dof_applies, jv_ms, t_region], dtype=torch.float64, device=dev)
-        tm = t.clone()
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dof_applies_all, jv_ms_max, t_region = float(t[0]), float(tm[1]), float(tm[2])
-    else:
-        dof_applies_all, jv_ms_max = dof_applies, jv_ms
+    dof_applies_all, jv_ms_max, t_region = aggregate_replicas(dof_applies, jv_ms, t_region, world, dev)
     value = dof_applies_all / (jv_ms_max / 1e3) / 1e9
 
     # ---- CN steps, plain FP64 (same tolerance, same start)
