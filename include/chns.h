@@ -98,7 +98,8 @@ typedef struct {
   int jacvec_calls;
   double residual_ms;              /* device time of the FP64 residual applies */
   int residual_calls;
-  double precond_ms;               /* host time of building the block-Jacobi preconditioner */
+  double precond_ms;               /* host time of building the preconditioner (block-Jacobi and
+                                      coarse space); 0 when a previous build was reused */
   int fp64_newton_its;             /* CHNS_FP32_BULK: Newton iterations finished with FP64 J.w */
 } chns_step_stats;
 
@@ -112,7 +113,9 @@ typedef struct {
  * be 2:1 balanced across faces, edges and corners (Sec. 4 "2:1 Balancing");
  * otherwise CHNS_ERR_MESH.  Colours the elements so that elements of one
  * colour touch disjoint node sets (hanging constraints included), which
- * makes the scatter-add free of atomics and deterministic. */
+ * makes the residual's scatter-add free of atomics and deterministic, and
+ * builds the node gather lists that sum the element-local J.w contributions
+ * of each node in a fixed order. */
 chns_status chns_mesh_create(int dim, int64_t n_leaves, const uint8_t *level,
                              const uint32_t *anchor, int max_level, const double lo[3],
                              const double hi[3], chns_mesh **out);
@@ -161,14 +164,16 @@ chns_status chns_init_mu(const chns_mesh *mesh, const chns_params *params, doubl
  * right-preconditioned FGMRES(m) with nodal block-Jacobi plus, optionally, an
  * additive coarse-space correction P (R J P)^{-1} R on a uniform coarse
  * octree level (R = P^T, P trilinear).  The residual and
- * the Newton update are double; with CHNS_FP32_BULK the Krylov J.w and
- * preconditioner run in float and the Gram-Schmidt inner products and norms
- * stay double (iterative refinement by the outer double residual); once a
- * float-Krylov Newton iteration cuts ||F|| by less than 10x, the remaining
- * iterations apply J in double with the float preconditioner promoted.  U_np1
- * receives the result (may not alias U_n).  stats (host, nullable).  Setting
- * the environment variable CHNS_TRACE=1 prints each Newton iteration to
- * stderr. */
+ * the Newton update are double; with CHNS_FP32_BULK the Krylov basis, J.w,
+ * Gram-Schmidt and preconditioner run in float (dot products summed per
+ * block in float, across blocks in double), refined by the outer double
+ * residual; once a float-Krylov Newton iteration cuts ||F|| by less than
+ * 10x, the remaining iterations apply J in double with the float
+ * preconditioner promoted.  Each Arnoldi step is replayed as a CUDA graph
+ * captured at its first use (CHNS_NO_GRAPHS=1 launches kernel by kernel).
+ * U_np1 receives the result (may not alias U_n).  stats (host, nullable).
+ * Setting the environment variable CHNS_TRACE=1 prints each Newton
+ * iteration to stderr.  A mesh is used by one host thread at a time. */
 chns_status chns_step(const chns_mesh *mesh, const chns_params *params,
                       const chns_solver_opts *opts, const double *U_n, const double *U_nm1,
                       const double *forcing, const double *bc, double *U_np1,

@@ -1,5 +1,6 @@
-// Krylov vector kernels (FGMRES with classical Gram-Schmidt applied twice),
-// nodal block-Jacobi preconditioner, deterministic double reductions.
+// Krylov vector kernels (FGMRES with classical Gram-Schmidt, a second pass on
+// a device flag), nodal block-Jacobi probing and inversion, deterministic
+// reductions (element-precision partials, one double sum per result).
 #include <algorithm>
 #include <cstdint>
 
@@ -84,21 +85,11 @@ __device__ __forceinline__ void sum_rows(const T *partial, int nrows, double *re
   }
 }
 
-// res[k] = sum_b partial[k * nblocks + b] (double, fixed order), k < nv.
-// Skipped (res[k] = 0) when flag is given and *flag == 0.  Optional outputs
-// for a squared norm (nv == 1): scale = 1/sqrt(res) in P (0 if res <= 0) and
-// the DGKS flag = (res < 1e-4 * before): the first projection removed more
-// than 99.99% of |w|^2, so a second Gram-Schmidt pass is needed.
+// res[k] = sum_b partial[k * nblocks + b] (double, fixed order), k < nv
 template <typename P>
-__global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int nv, double *__restrict__ res,
-                               const int *__restrict__ flag, P *__restrict__ scale,
-                               const double *__restrict__ before, int *__restrict__ flag_out) {
+__global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int nv, double *__restrict__ res) {
   const int k = blockIdx.x;
   if (k >= nv) return;
-  if (flag && *flag == 0) {
-    if (threadIdx.x == 0) res[k] = 0.0;
-    return;
-  }
   double s = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += double(partial[(int64_t)k * nblocks + b]);
   __shared__ double sh[kB / 32];
@@ -109,8 +100,6 @@ __global__ void k_sum_partials(const P *__restrict__ partial, int nblocks, int n
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
     res[k] = t;
-    if (scale) *scale = t > 0.0 ? P(1.0 / sqrt(t)) : P(0);
-    if (flag_out) *flag_out = (t < 1e-4 * before[0]) ? 1 : 0;
   }
 }
 
@@ -374,7 +363,7 @@ template void vec_multidot<double>(const double *, int64_t, int, const double *,
 
 void vec_dot(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st) {
   k_dot<<<kRedBlocks, kB, 0, st>>>(x, y, n, partial);
-  k_sum_partials<double><<<1, kB, 0, st>>>(partial, kRedBlocks, 1, res, nullptr, nullptr, nullptr, nullptr);
+  k_sum_partials<double><<<1, kB, 0, st>>>(partial, kRedBlocks, 1, res);
   note_launches(2);
 }
 
