@@ -547,12 +547,6 @@ __global__ void k_prep(const double *__restrict__ Un, const double *__restrict__
   }
 }
 
-template <typename T>
-__global__ void k_cast(const double *__restrict__ x, int64_t n, T *__restrict__ y) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    y[i] = T(x[i]);
-}
-
 // y[i] = sum over the slots of node i of weight * E[slot] (fixed order), then
 // the constrained rows: y = w on wall velocities and the pinned pressure.
 // The slots of a node are fetched eight at a time (independent loads), then
@@ -731,13 +725,6 @@ void launch_prep(const chns_mesh *m, const double *Un, const double *Uo, T *ut, 
 }
 template void launch_prep<float>(const chns_mesh *, const double *, const double *, float *, float *, cudaStream_t);
 template void launch_prep<double>(const chns_mesh *, const double *, const double *, double *, double *, cudaStream_t);
-
-template <typename T>
-void launch_cast(const double *x, int64_t n, T *y, cudaStream_t st) {
-  k_cast<T><<<grid_nodes(n), kBlock, 0, st>>>(x, n, y);
-  note_launches(1);
-}
-template void launch_cast<float>(const double *, int64_t, float *, cudaStream_t);
 
 namespace {
 template <int D, typename T, int MODE, bool HASF, typename O>

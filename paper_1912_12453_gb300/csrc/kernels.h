@@ -12,8 +12,6 @@ namespace chns {
 
 template <typename T>
 void launch_prep(const chns_mesh *m, const double *Un, const double *Uo, T *ut, T *dl, cudaStream_t st);
-template <typename T>
-void launch_cast(const double *x, int64_t n, T *y, cudaStream_t st);
 void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
                      const double *f, double *F, cudaStream_t st);
 template <typename T>

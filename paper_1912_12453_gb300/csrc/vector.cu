@@ -325,25 +325,6 @@ __global__ void k_invert_blocks(T *__restrict__ B, int64_t n_nodes, int *__restr
     for (int c = 0; c < NF; ++c) B[(a * NF + r) * NF + c] = T(M[r][NF + c]);
 }
 
-// z = Binv v  (all in T)
-template <typename T, int NF>
-__global__ void __launch_bounds__(kB) k_block_apply(const T *__restrict__ Binv, const T *__restrict__ v,
-                                                    T *__restrict__ z, int64_t n_nodes) {
-  for (int64_t a = blockIdx.x * int64_t(kB) + threadIdx.x; a < n_nodes; a += int64_t(gridDim.x) * kB) {
-    T x[NF];
-#pragma unroll
-    for (int c = 0; c < NF; ++c) x[c] = v[a * NF + c];
-    const T *b = Binv + a * NF * NF;
-#pragma unroll
-    for (int r = 0; r < NF; ++r) {
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < NF; ++c) s += b[r * NF + c] * x[c];
-      z[a * NF + r] = s;
-    }
-  }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -463,13 +444,5 @@ void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, cudaStream_t st) {
 }
 template void invert_blocks<float>(float *, int64_t, int, int *, cudaStream_t);
 template void invert_blocks<double>(double *, int64_t, int, int *, cudaStream_t);
-
-template <typename T>
-void block_apply(const T *Binv, const T *v, T *z, int64_t n_nodes, int nf, cudaStream_t st) {
-  if (nf == 5) { k_block_apply<T, 5><<<grid_n(n_nodes), kB, 0, st>>>(Binv, v, z, n_nodes); note_launches(1); }
-  else { k_block_apply<T, 6><<<grid_n(n_nodes), kB, 0, st>>>(Binv, v, z, n_nodes); note_launches(1); }
-}
-template void block_apply<float>(const float *, const float *, float *, int64_t, int, cudaStream_t);
-template void block_apply<double>(const double *, const double *, double *, int64_t, int, cudaStream_t);
 
 }  // namespace chns

@@ -45,7 +45,5 @@ template <typename T>
 void probe_get(const int32_t *nodes, int64_t cnt, int nf, int f, const T *y, T *B, cudaStream_t st);
 template <typename T>
 void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, cudaStream_t st);
-template <typename T>
-void block_apply(const T *Binv, const T *v, T *z, int64_t n_nodes, int nf, cudaStream_t st);
 
 }  // namespace chns
