@@ -476,3 +476,36 @@ def test_mms_spatial_rates_3d():
     rates = np.log2(errs[:-1] / errs[1:])
     assert np.all(rates[-1, 4:] > 1.6), rates
     assert np.all(rates[-1, 0:2] > 1.6), rates
+
+
+@pytest.mark.slow
+def test_mms_temporal_rate_phi_2d():
+    """Crank-Nicolson in time (Sec. 3.1): with the Sec. 5.1 manufactured
+    solution on a fixed mesh, phi at T = 0.8 computed with 4, 8, 16, 32 steps
+    converges at second order in time, as in the paper's temporal study of
+    phi.  Successive differences cancel the spatial error.  (v, p and mu are
+    not pinned this way: tau_m contains 4/dt^2, so the stabilised spatial
+    operator itself changes with dt, and p, mu enter the scheme only through
+    their CN averages.)"""
+    pytest.importorskip("sympy")
+    import dataclasses
+    from tests.mms import mms_functions
+    prm = W.Params(2, 1e-3, 1.0, 10.0, 1.0, 3.0, 1.0, 0.85, 0.5)
+    exact, forc = mms_functions(2, prm)
+    m = O.OracleMesh(W.uniform_leaves(2, 4))
+    rows = m.constrained_rows()
+    T, phis = 0.8, []
+    for nsteps in (4, 8, 16, 32):
+        dt = T / nsteps
+        p = dataclasses.replace(prm, dt=dt)
+        U, t = exact(m.coords, 0.0).reshape(-1), 0.0
+        for _ in range(nsteps):
+            f = forc(m.coords, t + dt / 2).reshape(-1)
+            g = np.zeros(m.n_dof)
+            g[rows] = exact(m.coords, t + dt).reshape(-1)[rows]
+            U, _ = m.step(p, U, rtol=1e-12, f=f, g=g)
+            t += dt
+        phis.append(U.reshape(-1, m.nf)[:, 3].copy())
+    d = [np.linalg.norm(phis[i] - phis[i + 1]) for i in range(3)]
+    rates = [math.log2(d[i] / d[i + 1]) for i in range(2)]
+    assert all(r > 1.7 for r in rates), rates
