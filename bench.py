@@ -1,27 +1,37 @@
 #!/usr/bin/env python
 """Benchmark of the matrix-free CN-VMS CHNS hot path on one GB300 (or N replicas).
 
-Workload: the 3D droplet on a uniform level-6 octree (64^3 trilinear hexes,
-274,625 nodes x 6 unknowns = 1,647,750 DoF), droplet radius 0.15 at
+Headline workload: the 3D droplet on a uniform level-6 octree (64^3 trilinear
+hexes, 274,625 nodes x 6 unknowns = 1,647,750 DoF), droplet radius 0.15 at
 (0.5, 0.5, 0.3), Cn 0.02, Re 100, We 50, Pe 1/Cn, Fr 1, density and viscosity
 ratios 1e-2, dt 5e-4, synthetic initial data.
 
 One timed step = one Crank-Nicolson step through the whole hot path: the FP64
-residual, the nodal block-Jacobi build, FGMRES with the FP32 element J.w and
-FP64 Gram-Schmidt, the FP64 Newton update, and the energy / mass diagnostics.
+residual, the preconditioner (rebuilt once per --precond-steps steps, inside
+the timed steps), FGMRES with the FP32 element J.w, FP32 Krylov basis and
+Gram-Schmidt (block sums in float, the sum over blocks in double), the FP64
+Newton update, and the energy / mass diagnostics.
 
 Reported value: Jacobian-apply throughput (GDoF/s = n_dof / mean J.w time) of
 the FP32-bulk applies inside the timed CN steps, from CUDA events the library
 records on the launching stream.  Also reported: seconds per CN step for the
-FP32-bulk mixed path and the plain FP64 path at the same Newton tolerance, an
-apply sweep over 100 seeded perturbation vectors (L2 flushed between applies),
-the end-to-end rate through host buffers, and the oracle timed on the host.
+FP32-bulk mixed path and the plain FP64 path at the same Newton tolerance
+(with per-field differences of the two solutions), an apply sweep over 100
+seeded perturbation vectors (L2 flushed between applies), the end-to-end rate
+through host buffers, the same step comparison on further workloads
+(--extra, default the adaptive 3D bubble), and the oracle timed on the host
+cores (single thread and all cores).
+
+--profile-applies N only builds the mesh and runs N operator applies (for a
+profiler; no JSON line).
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -37,18 +47,27 @@ from paper_1912_12453_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Jacobian-apply GDoF/s and s per CN step, FP32-mixed vs FP64 at equal residual"
 WORKLOAD = "droplet3d_l6"
-# FP32 operations per element of one 3D J.w apply, counted by ncu on the
-# element kernel (thread-level FADD + FMUL + 2 x FFMA: 3.547e8 per 32,768
-# elements of the level-6 droplet).
-JV_FLOP_PER_ELEM_3D = 10825
-# DRAM bytes of one J.w apply (element kernel + node gather) of the level-6
-# droplet mesh, read + write, from one ncu capture with --cache-control none
-# after an L2 flush.  Valid for the kernels as profiled; null for other meshes.
-JV_TRAFFIC_PER_APPLY = {262144: 45_309_312 + 90_735_360}
-# FP32 FMA-pipe peak measured on GB300 by paper_1912_12453_gb300/probes/fma_peak.cu
-# (independent FMA chains on all SMs); the derived 152 x 128 x 2 x 2.07 GHz is 80.5.
-FP32_PEAK_TFLOPS = 78.37
-HBM_PEAK_FALLBACK = 6800.0
+DESCRIPTION = {
+    "droplet2d_l5": "2D droplet, uniform quadtree level 5 (32^2 quads, 1,089 nodes, 5,445 DoF), Cn 0.04, Re 35, "
+                    "We 125, ratios 0.1, dt 1e-3",
+    "droplet3d_l6": "3D droplet, uniform octree level 6 (64^3 hexes, 274,625 nodes, 1,647,750 DoF), Cn 0.02, "
+                    "Re 100, We 50, ratios 1e-2, dt 5e-4",
+    "bubble3d_l5_9": "3D rising bubble, adaptive octree levels 5-9 in |phi| < 0.9, 2:1 balanced, hanging nodes, "
+                     "Cn 0.01, Re 35, We 1, ratios 1e-3 / 1e-2, dt 2.5e-4",
+    "merge3d_l6_10": "3D merging droplets, adaptive octree levels 6-10 in |phi| < 0.9, Cn 0.005, Re 100, We 10, "
+                     "ratios 1e-3 / 1e-2, dt 1e-4",
+}
+# FP32 operations per leaf of one J.w apply of the element kernel, counted by
+# ncu on k_element<3, float, J.w> (thread-level FADD + FMUL + 2 x FFMA).  The
+# kernel does the same arithmetic for every leaf of every 3D mesh (hanging
+# corners only add gather loads), so the count holds for any 3D mesh while the
+# kernel is unchanged.
+JV_FLOP_PER_LEAF = {3: 10825}
+# DRAM bytes (read + write) of one J.w apply, element kernel + node gather,
+# from one ncu capture of the named workload; valid for that mesh only.
+JV_TRAFFIC_PER_APPLY = {"droplet3d_l6": 45_309_312 + 90_735_360}
+# Algorithmic bytes of one FP32 J.w apply per node (read U~, dU and w, write y)
+JV_ALG_BYTES_PER_NODE = {3: 4 * (6 + 4 + 6 + 6), 2: 4 * (5 + 3 + 5 + 5)}
 
 
 def log(*a):
@@ -61,6 +80,18 @@ def _measured_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+def measure_fma_peaks():
+    """FP32 / FP64 FMA-pipe peaks of this GPU, measured now (libchns_peak.so)."""
+    from paper_1912_12453_gb300 import build
+    L = ctypes.CDLL(build.PEAK_OUT)
+    L.chns_peak_fma.restype = ctypes.c_int
+    L.chns_peak_fma.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    if L.chns_peak_fma(ctypes.byref(f32), ctypes.byref(f64)) != 0:
+        raise RuntimeError("FMA peak probe failed")
+    return f32.value, f64.value
 
 
 class ClockSampler:
@@ -144,51 +175,171 @@ def _gpu_index(local_rank: int) -> int:
     return local_rank
 
 
-def cpu_oracle_japply(wl, n_applies: int):
-    """The oracle's J.w (single-threaded FP64 C++) on the full mesh."""
+# ---------------------------------------------------------------- the oracle on the host
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "arch": platform.machine()}
+
+
+def _oracle_inputs(wl):
     from oracle import oracle as O
     om = O.OracleMesh(wl.leaves)
     U0 = W.initial_state(om.coords, wl).reshape(-1)
     w = W.perturbation(om.n_nodes, om.nf, 1)[0].reshape(-1)
-    U1 = U0 + 1e-2 * w
-    om.jacvec(wl.params, U1, U0, w)  # warm-up (page-in)
+    return om, U0 + 1e-2 * w, U0, w
+
+
+def _time_applies(fn, repeats, warmup):
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def cpu_baseline(wl_main, threads):
+    """The oracle as it stands, on the host cores: J.w applies of the
+    headline mesh on one thread and on all cores (median of 20 after 3
+    warm-ups on all cores; 3 after 1 on one thread, the single-thread apply
+    taking seconds), J.w applies of the 2D droplet (median of 20 after 3,
+    one thread), and one oracle CN step of the 2D droplet (one thread,
+    sparse direct Newton to 1e-10)."""
+    out = dict(host_info())
+    om, U1, U0, w = _oracle_inputs(wl_main)
+    ts1 = _time_applies(lambda: om.jacvec(wl_main.params, U1, U0, w), 3, 1)
+    tsn = _time_applies(lambda: om.jacvec_threads(wl_main.params, U1, U0, w, threads), 20, 3)
+    out["main"] = {"workload": wl_main.name, "n_dof": om.n_dof,
+                   "jacvec_1thread_s": float(np.median(ts1)), "jacvec_1thread_GDoFs": om.n_dof / np.median(ts1) / 1e9,
+                   "jacvec_allcores_s": float(np.median(tsn)), "jacvec_allcores_GDoFs": om.n_dof / np.median(tsn) / 1e9,
+                   "threads": threads, "repeats": {"1thread": 3, "allcores": 20}}
+    wl1 = W.workload("droplet2d_l5")
+    o1, V1, V0, w1 = _oracle_inputs(wl1)
+    t1 = _time_applies(lambda: o1.jacvec(wl1.params, V1, V0, w1), 20, 3)
+    r1 = _time_applies(lambda: o1.residual(wl1.params, V1, V0), 20, 3)
+    Ui = o1.init_mu(wl1.params, V0)
     t0 = time.perf_counter()
-    for _ in range(n_applies):
-        om.jacvec(wl.params, U1, U0, w)
-    dt = (time.perf_counter() - t0) / n_applies
-    return om.n_dof, dt
+    _, st = o1.step(wl1.params, Ui, rtol=1e-10)
+    out["droplet2d_l5"] = {"n_dof": o1.n_dof, "jacvec_1thread_s": float(np.median(t1)),
+                           "residual_1thread_s": float(np.median(r1)),
+                           "cn_step_1thread_s": time.perf_counter() - t0, "cn_step_newton_its": st["newton_its"]}
+    out["main_cn_step"] = ("not run: the oracle's Newton uses a sparse direct factorisation of the full Jacobian, "
+                           "which for the 1.65M-DoF 3D mesh exceeds the benchmark's few-minute cap")
+    return out, om.n_dof / np.median(tsn) / 1e9
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: each step is one J.w apply of the full
-    workload on one host core (a bounded sample of the J.w applies the GPU
-    arm runs)."""
+    """The oracle as the reference arm: each step is one J.w apply of the
+    headline workload on all host cores (the oracle's element loop, elements
+    grouped by its own colouring)."""
     if rank != 0:
         return
     wl = W.workload(WORKLOAD)
-    from oracle import oracle as O
-    om = O.OracleMesh(wl.leaves)
-    U0 = W.initial_state(om.coords, wl).reshape(-1)
-    w = W.perturbation(om.n_nodes, om.nf, 1)[0].reshape(-1)
-    U1 = U0 + 1e-2 * w
+    threads = os.cpu_count() or 1
+    om, U1, U0, w = _oracle_inputs(wl)
     for _ in range(args.warmup):
-        om.jacvec(wl.params, U1, U0, w)
+        om.jacvec_threads(wl.params, U1, U0, w, threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        om.jacvec(wl.params, U1, U0, w)
+        om.jacvec_threads(wl.params, U1, U0, w, threads)
     T = time.perf_counter() - t0
     value = om.n_dof * args.steps / T / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "3D droplet, uniform octree level 6 (64^3 hexes, "
-                                                   "1,647,750 DoF)", "l2": "host"},
-        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "GDoF/s", "cores": 1,
-                         "sample": f"{args.steps} oracle J.w applies of the full mesh, one host thread"},
+        "data": "synthetic", "config": {"workload": DESCRIPTION[WORKLOAD], "l2": "host"},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "GDoF/s", "cores": threads,
+                         "sample": f"{args.steps} oracle J.w applies of the full mesh ({om.n_dof} DoF), "
+                                   f"{threads} host threads", **host_info()},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU side
+
+def field_diffs(a, b, nf, dim):
+    """Per-field relative 2-norm differences of two states (v, p, phi, mu)."""
+    import torch
+    A = a.reshape(-1, nf)
+    B = b.reshape(-1, nf)
+    names = [f"v{i + 1}" for i in range(dim)] + ["p", "phi", "mu"]
+    out = {}
+    for k, n in enumerate(names):
+        den = float(torch.linalg.vector_norm(B[:, k]))
+        out[n] = float(torch.linalg.vector_norm(A[:, k] - B[:, k])) / den if den > 0 else None
+    return out
+
+
+def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier):
+    """FP32-bulk mixed vs plain FP64 CN steps from the same state, both to the
+    same Newton tolerance: seconds per step (CUDA events), iteration counts,
+    per-field solution differences."""
+    import torch
+    out = {}
+    finals = {}
+    for name, opts in (("fp32_mixed", opts32), ("fp64", opts64)):
+        Ua, Ub = U0.clone(), torch.empty_like(U0)
+        chns.step(mesh, wl.params, Ua, Ub, opts)  # warm-up (builds graphs and the preconditioner)
+        Ua.copy_(U0)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record()
+        for _ in range(steps):
+            stats.append(chns.step(mesh, wl.params, Ua, Ub, opts))
+            Ua, Ub = Ub, Ua
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        finals[name] = Ua.clone()
+        out[name] = {"s_per_step": ms / 1e3, "newton_its": [s["newton_its"] for s in stats],
+                     "krylov_its": [s["krylov_its_total"] for s in stats],
+                     "res_rel": [s["res_final"] / s["res0"] for s in stats],
+                     "jacvec_ms_per_apply": sum(s["jacvec_ms"] for s in stats) / max(1, sum(s["jacvec_calls"] for s in stats)),
+                     "precond_ms_per_step": float(np.mean([s["precond_ms"] for s in stats])),
+                     "fp64_newton_its": [s["fp64_newton_its"] for s in stats]}
+        log(name, wl.name, f"{ms:.1f} ms/step", out[name]["newton_its"], out[name]["krylov_its"])
+    out["speedup_fp32_mixed_over_fp64"] = out["fp64"]["s_per_step"] / out["fp32_mixed"]["s_per_step"]
+    out["rel_diff_fp32_vs_fp64_per_field"] = field_diffs(finals["fp32_mixed"], finals["fp64"], mesh.nf, mesh.dim)
+    out["steps"] = steps
+    return out
+
+
+def profile_applies(args):
+    """Mesh, initial state, then --profile-applies operator applies with an L2
+    flush before each: a short command for a profiler to capture."""
+    import torch
+    from paper_1912_12453_gb300 import build, chns
+    build.build()
+    wl = W.workload(args.workload)
+    mesh = chns.Mesh(wl.leaves)
+    U0 = torch.from_numpy(W.initial_state(mesh.coords, wl).reshape(-1)).cuda()
+    U1 = U0 + 1e-2 * torch.from_numpy(W.perturbation(mesh.n_nodes, mesh.nf, 1)[0].reshape(-1)).cuda()
+    dt = torch.float32 if args.profile_precision == "fp32" else torch.float64
+    w = torch.from_numpy(W.perturbation(mesh.n_nodes, mesh.nf, 2)[1].reshape(-1)).to("cuda", dt)
+    y = torch.empty_like(w)
+    F = torch.empty_like(U0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for r in range(args.profile_applies):
+        flush.fill_(float(r))
+        chns.jacvec(mesh, wl.params, U1, U0, w, out=y, precision=args.profile_precision)
+        if args.profile_residual:
+            chns.residual(mesh, wl.params, U1, U0, out=F)
+    torch.cuda.synchronize()
+    log(f"{args.profile_applies} applies on {mesh.n_elem} elements ({mesh.n_dof} DoF) done")
 
 
 def main():
@@ -200,15 +351,20 @@ def main():
     ap.add_argument("--apply-vectors", type=int, default=100)
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 CN steps (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-applies", type=int, default=2)
     ap.add_argument("--newton-rtol", type=float, default=1e-9)
     ap.add_argument("--precond-steps", type=int, default=5,
                     help="CN steps one preconditioner build serves (1: rebuilt every step); with the "
                          "defaults one rebuild falls inside the 5 timed steps")
-    ap.add_argument("--workload", default=WORKLOAD,
-                    help="droplet3d_l6 (the metric's configuration), droplet2d_l5 or bubble3d_l5_9")
+    ap.add_argument("--workload", default=WORKLOAD, help="headline workload (droplet3d_l6)")
+    ap.add_argument("--extra", default="bubble3d_l5_9",
+                    help="comma-separated further workloads for the FP32-vs-FP64 step comparison "
+                         "(bubble3d_l5_9, merge3d_l6_10; empty: none)")
+    ap.add_argument("--extra-steps", type=int, default=2)
     ap.add_argument("--krylov-max-it", type=int, default=400)
     ap.add_argument("--krylov-restart", type=int, default=64)
+    ap.add_argument("--profile-applies", type=int, default=0)
+    ap.add_argument("--profile-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--profile-residual", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -216,6 +372,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_applies:
+        profile_applies(args)
         return
 
     import torch
@@ -236,6 +395,9 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    fp32_peak, fp64_peak = measure_fma_peaks()
+    log(f"FMA peaks: FP32 {fp32_peak:.2f} TFLOP/s, FP64 {fp64_peak:.3f} TFLOP/s")
 
     wl = W.workload(args.workload)
     prm = wl.params
@@ -272,11 +434,10 @@ def main():
         return float(np.mean(times)), float(np.median(times))
 
     log(f"mesh: {mesh.n_elem} elements, {n_dof} DoF, {mesh.n_colours} colours")
-    jv32_mean, jv32_med = sweep("fp32")
-    log(f"apply sweep fp32 J.w {jv32_mean:.3f} ms")
-    jv64_mean, jv64_med = sweep("fp64", "jacvec") if nvec > 0 else (None, None)
+    jv32_mean, _ = sweep("fp32") if nvec > 0 else (None, None)
+    jv64_mean, _ = sweep("fp64", "jacvec") if nvec > 0 else (None, None)
     res64_mean, _ = sweep("fp64", "residual") if nvec > 0 else (None, None)
-    log(f"apply sweep fp64 J.w {jv64_mean} ms, residual {res64_mean} ms")
+    log(f"apply sweep: fp32 J.w {jv32_mean} ms, fp64 J.w {jv64_mean} ms, fp64 residual {res64_mean} ms")
 
     # ---- CN steps, FP32-bulk mixed (timed region)
     opts32 = chns.SolverOpts.make(precision="fp32", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
@@ -320,6 +481,7 @@ def main():
     k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
     stats64 = []
     step64_ms = None
+    diff = None
     if k64 > 0:
         Ua.copy_(U0)
         chns.step(mesh, prm, Ua, Ub, opts64)  # warm-up
@@ -329,22 +491,19 @@ def main():
         e0.record(stream)
         for _ in range(k64):
             stats64.append(chns.step(mesh, prm, Ua, Ub, opts64))
-            log("fp64 step", {k: stats64[-1][k] for k in ("newton_its", "krylov_its_total", "seconds")})
             Ua, Ub = Ub, Ua
         e1.record(stream)
         barrier()
         step64_ms = e0.elapsed_time(e1) / k64
-        U64 = Ua.clone()
-        diff = float(torch.linalg.vector_norm(U32 - U64) / torch.linalg.vector_norm(U64)) if k64 == args.steps else None
-    else:
-        diff = None
+        log("fp64 steps", [{k: st[k] for k in ("newton_its", "krylov_its_total", "seconds")} for st in stats64])
+        if k64 == args.steps:
+            diff = field_diffs(U32, Ua, mesh.nf, mesh.dim)
 
     # ---- end to end through host buffers: H2D of U_n, the step, D2H of U_{n+1}
     host_in = torch.from_numpy(U0h.copy()).pin_memory()
     host_out = torch.empty(n_dof, dtype=torch.float64).pin_memory()
     Ud = torch.empty(n_dof, dtype=torch.float64, device=dev)
-    chns.init_mu(mesh, prm, U0)  # host_in holds mu from the device projection
-    host_in.copy_(U0.cpu())
+    host_in.copy_(U0.cpu())  # mu from the device projection
     barrier()
     e_calls = 0
     t0 = time.perf_counter()
@@ -363,48 +522,80 @@ def main():
     peaks = _measured_peaks()
     jv_apply_ms = jv_ms / max(jv_calls, 1)
     roof = None
-    if JV_FLOP_PER_ELEM_3D:
-        ach = JV_FLOP_PER_ELEM_3D * mesh.n_elem / (jv_apply_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": JV_TRAFFIC_PER_APPLY.get(mesh.n_elem) if mesh.dim == 3 else None,
-                "per": f"one J.w apply (element kernel over {mesh.n_elem} leaves + node gather, "
-                       f"{JV_FLOP_PER_ELEM_3D} flop/element)",
+    fpl = JV_FLOP_PER_LEAF.get(mesh.dim)
+    if fpl:
+        ach = fpl * mesh.n_elem / (jv_apply_ms / 1e3) / 1e12
+        traffic = JV_TRAFFIC_PER_APPLY.get(args.workload)
+        alg_bytes = JV_ALG_BYTES_PER_NODE[mesh.dim] * mesh.n_nodes
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": traffic,
+                "per": f"one J.w apply inside the timed CN steps (element kernel over {mesh.n_elem} leaves + node "
+                       f"gather), {fpl} FP32 flop per leaf (ncu count of the element kernel)",
                 "kernel": "k_element<3,float,J.w> + k_gather_nodes<3,float>",
-                "peak_source": "measured FP32 FMA pipe (probes/fma_peak.cu)",
-                "hbm_gbs_achieved": (JV_TRAFFIC_PER_APPLY.get(mesh.n_elem, 0) / (jv_apply_ms / 1e3) / 1e9)
-                if mesh.dim == 3 else None}
+                "peak_source": "FP32 FMA pipe measured in this run (libchns_peak.so), of measured",
+                "algorithmic_bytes_per_apply": alg_bytes,
+                "hbm_gbs_algorithmic": alg_bytes / (jv_apply_ms / 1e3) / 1e9,
+                "hbm_frac_algorithmic": alg_bytes / (jv_apply_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
+                if peaks.get("hbm_gbs") else None}
+
+    # ---- further workloads: FP32-bulk vs FP64 steps at the same tolerance
+    extra = {}
+    for name in [x for x in args.extra.split(",") if x]:
+        try:
+            wx = W.workload(name)
+            mx = chns.Mesh(wx.leaves)
+            Ux = torch.from_numpy(W.initial_state(mx.coords, wx).reshape(-1)).to(dev)
+            chns.init_mu(mx, wx.params, Ux)
+            log(f"{name}: {mx.n_elem} leaves, {mx.n_dof} DoF, {mx.n_hanging} hanging nodes")
+            r = compare_steps(chns, wx, mx, Ux, args.extra_steps, opts32, opts64, dev, barrier)
+            r.update({"workload": DESCRIPTION.get(name, name), "leaves": mx.n_elem, "n_dof": mx.n_dof,
+                      "hanging_nodes": mx.n_hanging, "newton_rtol": args.newton_rtol})
+            extra[name] = r
+            mx.close()
+            del Ux
+            torch.cuda.empty_cache()
+        except Exception as ex:  # report, do not hide: the line says what failed
+            extra[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            log(name, "failed:", ex)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        log("cpu baseline: oracle J.w")
-        nd, t_cpu = cpu_oracle_japply(wl, args.cpu_applies)
-        cpu = {"value": nd / t_cpu / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_applies} oracle J.w applies of the full mesh ({nd} DoF), one host thread"}
+        log("cpu baseline: oracle applies and a 2D CN step")
+        threads = os.cpu_count() or 1
+        detail, val_all = cpu_baseline(wl, threads)
+        cpu = {"value": val_all, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
+               "sample": f"oracle J.w of the full {args.workload} mesh on {threads} host threads, median of 20 "
+                         f"after 3 warm-ups; details (single thread, 2D droplet applies and CN step) in 'detail'",
+               "detail": detail}
 
     if rank == 0:
+        steps_first = {"newton_its": [s["newton_its"] for s in stats32],
+                       "krylov_its": [s["krylov_its_total"] for s in stats32],
+                       "res_rel": [s["res_final"] / s["res0"] for s in stats32],
+                       "jacvec_ms_per_apply": jv_apply_ms,
+                       "residual_ms": sum(s["residual_ms"] for s in stats32) / max(1, sum(s["residual_calls"] for s in stats32)),
+                       "precond_ms_per_step": float(np.mean([s["precond_ms"] for s in stats32])),
+                       "s_per_step": step32_ms / 1e3}
+        basis_mb = (args.krylov_restart + 1) * n_dof * 4 / 1e6
         line = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step32_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "3D droplet, uniform octree level 6 (64^3 hexes, 274,625 nodes, "
-                                   "1,647,750 DoF), Cn 0.02, Re 100, We 50, ratios 1e-2, dt 5e-4",
-                       "precision": "FP32 element J.w + FP32 block-Jacobi inside FP64 Newton / FP64 Gram-Schmidt",
+            "config": {"workload": DESCRIPTION[args.workload],
+                       "precision": "FP32 element J.w, FP32 Krylov basis and Gram-Schmidt (products and block sums "
+                                    "in float, the sum over blocks in double), FP32 preconditioner, inside an FP64 "
+                                    "Newton iteration (FP64 residual and update)",
                        "newton_rtol": args.newton_rtol,
                        "krylov": f"FGMRES({args.krylov_restart})",
                        "preconditioner": f"nodal block-Jacobi + Galerkin coarse space (uniform level "
                                          f"min(3, coarsest leaf - 1)), built once per {args.precond_steps} CN steps "
                                          f"({sum(1 for s_ in stats32 if s_['precond_ms'] > 0)} builds inside the timed steps)",
-                       "l2": "step working set (Krylov basis 31 x 13 MB) > L2; apply sweep flushes L2",
+                       "l2": f"inputs larger than L2: the step's Krylov basis is {args.krylov_restart + 1} x "
+                             f"{n_dof * 4 / 1e6:.1f} MB = {basis_mb:.0f} MB of floats; the apply sweep flushes L2 "
+                             f"(256 MB write) before every apply",
                        "parallelism": f"replicas x{world}"},
             "cn_step": {
-                "fp32_mixed": {"s_per_step": step32_ms / 1e3,
-                               "newton_its": [s["newton_its"] for s in stats32],
-                               "krylov_its": [s["krylov_its_total"] for s in stats32],
-                               "res_rel": [s["res_final"] / s["res0"] for s in stats32],
-                               "jacvec_ms_per_apply": jv_apply_ms,
-                               "residual_ms": sum(s["residual_ms"] for s in stats32) / max(1, sum(s["residual_calls"] for s in stats32)),
-                               "precond_ms_per_step": float(np.mean([s["precond_ms"] for s in stats32]))},
+                "fp32_mixed": steps_first,
                 "fp64": None if not stats64 else {
                     "s_per_step": step64_ms / 1e3,
                     "newton_its": [s["newton_its"] for s in stats64],
@@ -412,20 +603,23 @@ def main():
                     "res_rel": [s["res_final"] / s["res0"] for s in stats64],
                     "jacvec_ms_per_apply": sum(s["jacvec_ms"] for s in stats64) / max(1, sum(s["jacvec_calls"] for s in stats64))},
                 "speedup_fp32_mixed_over_fp64": (step64_ms / step32_ms) if step64_ms else None,
-                "rel_diff_fp32_vs_fp64_solution": diff,
+                "rel_diff_fp32_vs_fp64_per_field": diff,
             },
-            "apply_sweep": {"vectors": nvec, "jacvec_fp32_ms": jv32_mean, "jacvec_fp32_GDoFs": n_dof / jv32_mean / 1e6,
+            "apply_sweep": {"vectors": nvec, "jacvec_fp32_ms": jv32_mean,
+                            "jacvec_fp32_GDoFs": n_dof / jv32_mean / 1e6 if jv32_mean else None,
                             "jacvec_fp64_ms": jv64_mean,
                             "jacvec_fp64_GDoFs": (n_dof / jv64_mean / 1e6) if jv64_mean else None,
                             "residual_fp64_ms": res64_mean,
                             "residual_fp64_GDoFs": (n_dof / res64_mean / 1e6) if res64_mean else None},
+            "extra_workloads": extra,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": n_dof * 8,
                     "d2h_bytes_per_step": n_dof * 8},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
-            "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "fp32_fma_tflops_measured": FP32_PEAK_TFLOPS},
+            "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "fp32_fma_tflops_measured_now": fp32_peak,
+                      "fp64_fma_tflops_measured_now": fp64_peak},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -50,8 +50,9 @@ typedef enum {
   CHNS_ERR_CUDA = 3,       /* a CUDA runtime call failed */
   CHNS_ERR_NONFINITE = 4,  /* NaN or Inf in a residual or Krylov norm */
   CHNS_ERR_NEWTON = 5,     /* Newton did not reach its tolerance in newton_max_it */
-  CHNS_ERR_KRYLOV = 6,     /* FGMRES breakdown or no progress */
-  CHNS_ERR_TIMEOUT = 7,    /* a bounded device-side wait ran out */
+  CHNS_ERR_KRYLOV = 6,     /* FGMRES breakdown, or a singular nodal / coarse block in the
+                              preconditioner */
+  /* 7 is not used: no kernel of this library waits on a device-side flag */
   CHNS_ERR_OOM = 8         /* device allocation failed */
 } chns_status;
 
@@ -70,6 +71,11 @@ typedef struct {
   double gravity[3];
 } chns_params;
 
+typedef enum {
+  CHNS_PC_TWO_LEVEL = 0,   /* nodal block-Jacobi + additive Galerkin coarse space (coarse_level) */
+  CHNS_PC_MULTIGRID = 1    /* geometric multigrid V-cycle over the octree levels (mg_* fields) */
+} chns_preconditioner;
+
 typedef struct {
   double newton_rtol;      /* stop when ||F||_2 <= newton_rtol ||F(initial guess)||_2 ... */
   double newton_atol;      /* ... or ||F||_2 <= newton_atol */
@@ -85,6 +91,29 @@ typedef struct {
   int coarse_level;        /* two-level preconditioner: coarse octree level L_c >= 1 (at most one
                               below the coarsest leaf); 0 = block-Jacobi only; -1 = automatic
                               (L_c = min(3, coarsest leaf level - 1), off if that is < 1) */
+  int use_graph;           /* 1: each Arnoldi step is captured once as a CUDA graph and replayed;
+                              0: launched kernel by kernel (same arithmetic, same results) */
+  chns_preconditioner preconditioner;
+  int mg_coarsest;         /* multigrid: uniform octree level of the coarsest mesh, solved exactly
+                              by a dense inverse (clamped to the coarsest leaf level); -1 = 2 in 3D,
+                              3 in 2D */
+  int mg_smooth;           /* multigrid: damped block-Jacobi sweeps before and after each coarse
+                              correction (1..8) */
+  double mg_omega;         /* multigrid: damping of the block-Jacobi sweeps (0 < omega <= 1) */
+  int block_iteration;     /* 0: coupled Newton on all fields; 1: the block iteration of Sec. 3.1
+                              (Fig. flowchart_block): Newton on the Navier-Stokes fields (v, p) with
+                              phi, mu frozen, then on the Cahn-Hilliard fields (phi, mu) with v, p
+                              frozen, repeated until a block iteration after the first changes no
+                              entry of (v, p, phi, mu) by more than block_tol */
+  double block_tol;        /* block iteration: tolerance on the max-norm change (the paper: 1e-4) */
+  int block_max_it;        /* block iteration: at most this many block iterations (else
+                              CHNS_ERR_NEWTON) */
+  int autotune;            /* 1: at its first FP32-bulk step a mesh (and each multigrid level)
+                              times every FP32 J.w schedule of the library (element-local buffer +
+                              node gather at several block shapes and register budgets, or element
+                              colours with in-place adds) and keeps the fastest; 0: the default
+                              schedule.  Results are identical up to the summation order of a
+                              node's contributions. */
 } chns_solver_opts;
 
 typedef struct {
@@ -101,6 +130,10 @@ typedef struct {
   double precond_ms;               /* host time of building the preconditioner (block-Jacobi and
                                       coarse space); 0 when a previous build was reused */
   int fp64_newton_its;             /* CHNS_FP32_BULK: Newton iterations finished with FP64 J.w */
+  int block_its;                   /* block iterations (0 with the coupled Newton); newton_its then
+                                      counts the Newton iterations of all sub-solves, and res_final is
+                                      the coupled residual of the result */
+  int jacvec_variant;              /* the mesh's FP32 J.w schedule (0 until autotuned) */
 } chns_step_stats;
 
 /* ---------------------------------------------------------------- meshes */
@@ -127,6 +160,25 @@ chns_status chns_mesh_info(const chns_mesh *mesh, int64_t *n_nodes, int64_t *n_d
 /* Integer coordinates (max_level resolution) of the independent nodes in the
  * library's numbering.  Host output xyz[n_nodes*dim]. */
 chns_status chns_mesh_node_coords(const chns_mesh *mesh, int64_t *xyz);
+
+/* Host-side validation of a built mesh (reads its device arrays back):
+ * elements of one colour touch disjoint sets of independent nodes, hanging
+ * parents expanded (so the residual's colour-by-colour scatter-add needs no
+ * atomics); every independent node's gather list holds exactly the (element,
+ * corner) slots that reach it, with weight 1 directly or 1/2 (edge) / 1/4
+ * (face) through a hanging corner, in increasing slot order; every hanging
+ * node has 2 or 4 independent parents.  CHNS_OK or CHNS_ERR_MESH with the
+ * first violation in chns_last_error(). */
+chns_status chns_mesh_check(const chns_mesh *mesh);
+
+/* The FP32 J.w schedule of a mesh (the autotuner's choice, see
+ * chns_solver_opts.autotune): variant in [0, 7) fixes it (and marks the mesh
+ * tuned); times_ms (host, nullable, 7 entries) receives the autotuner's
+ * median time per schedule, negative where none was measured.  Schedules:
+ * 0-3, 5, 6 element-local buffer + node gather with (block size, blocks per
+ * SM) = (128, 6), (256, 3), (64, 12), (128, 8), -, (128, 5), (128, 4); 4
+ * element colours with in-place adds.  variant = -1 only reads. */
+chns_status chns_mesh_jacvec_schedule(chns_mesh *mesh, int variant, int *current, double *times_ms);
 
 void chns_mesh_destroy(chns_mesh *mesh);
 
@@ -161,23 +213,44 @@ chns_status chns_init_mu(const chns_mesh *mesh, const chns_params *params, doubl
 
 /* One Crank-Nicolson step (Sec. 3.1, 3.5): Newton on F(U; U_n) = 0 from the
  * guess U_n (or 2 U_n - U_nm1 when U_nm1 is not NULL), each correction by
- * right-preconditioned FGMRES(m) with nodal block-Jacobi plus, optionally, an
- * additive coarse-space correction P (R J P)^{-1} R on a uniform coarse
- * octree level (R = P^T, P trilinear).  The residual and
+ * right-preconditioned FGMRES(m).  Preconditioners: CHNS_PC_TWO_LEVEL, nodal
+ * block-Jacobi plus, optionally, an additive coarse-space correction
+ * P (R J P)^{-1} R on a uniform coarse octree level (R = P^T, P trilinear);
+ * CHNS_PC_MULTIGRID, a V-cycle over the meshes obtained by repeatedly merging
+ * the finest leaves (each level applies the same J.w on its own leaves,
+ * linearised at the injected state; damped nodal block-Jacobi smoothing;
+ * transfers by Q1 interpolation with hanging constraints and its transpose;
+ * the coarsest uniform level solved by a dense inverse; the hierarchy is
+ * built at the first multigrid step of a mesh and kept).  The residual and
  * the Newton update are double; with CHNS_FP32_BULK the Krylov basis, J.w,
  * Gram-Schmidt and preconditioner run in float (dot products summed per
  * block in float, across blocks in double), refined by the outer double
  * residual; once a float-Krylov Newton iteration cuts ||F|| by less than
  * 10x, the remaining iterations apply J in double with the float
- * preconditioner promoted.  Each Arnoldi step is replayed as a CUDA graph
- * captured at its first use (CHNS_NO_GRAPHS=1 launches kernel by kernel).
- * U_np1 receives the result (may not alias U_n).  stats (host, nullable).
- * Setting the environment variable CHNS_TRACE=1 prints each Newton
- * iteration to stderr.  A mesh is used by one host thread at a time. */
+ * preconditioner promoted.  With opts->use_graph each Arnoldi step is
+ * replayed as a CUDA graph captured at its first use.  U_np1 receives the
+ * result (may not alias U_n).  stats (host, nullable).  Errors:
+ * CHNS_ERR_NONFINITE when a residual or Krylov norm is NaN/Inf (e.g. NaN in
+ * U_n), CHNS_ERR_NEWTON after newton_max_it iterations without reaching the
+ * tolerance, CHNS_ERR_KRYLOV on an FGMRES breakdown or a singular
+ * preconditioner block.  Setting the environment variable CHNS_TRACE=1
+ * prints each Newton iteration to stderr; CHNS_INJECT=krylov makes the next
+ * FGMRES report a breakdown (a host-side fault injection for tests of the
+ * caller's error handling).  A mesh is used by one host thread at a time. */
 chns_status chns_step(const chns_mesh *mesh, const chns_params *params,
                       const chns_solver_opts *opts, const double *U_n, const double *U_nm1,
                       const double *forcing, const double *bc, double *U_np1,
                       chns_step_stats *stats, void *stream);
+
+/* Number of Gauss points, over all leaves, at which the tau_m radicand of
+ * Sec. 3.4 (4/dt^2 + v~.G v~ + v~.G J~/(rho Pe) + C_I (eta/(rho Re))^2 G:G)
+ * falls below 4/dt^2 and is raised to it (v~.J~ < 0 can make it small or
+ * negative; the paper does not discuss the case).  Evaluated in double
+ * precision at U_new, U_old exactly as chns_residual evaluates tau_m.  count:
+ * host output; synchronises the stream. */
+chns_status chns_tau_floor_count(const chns_mesh *mesh, const chns_params *params,
+                                 const double *U_new, const double *U_old, int64_t *count,
+                                 void *stream);
 
 /* Diagnostics with the same 2^dim Gauss rule (host outputs, synchronises):
  * energy functional (Eq. energy_functional, gravity potential (1/Fr) rho(phi*)

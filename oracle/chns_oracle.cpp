@@ -39,6 +39,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -94,6 +95,9 @@ struct Mesh {
   int64_t origin = -1;
   int64_t n_hanging = 0;
   std::string err;
+  // element colours for the threaded J.w (built on first use): elements of
+  // one colour share no independent node through P
+  std::vector<std::vector<int64_t>> colour_elems;
 };
 
 // canonical key: z slowest, x fastest
@@ -273,9 +277,11 @@ Field<T> interp(int dim, const Basis& B, const T* nodal, int stride, int comp) {
 // ---------------------------------------------------------------- element residual
 // un, uo: local nodal values (nc x nf) of U^{k+1}, U^k; f: local nodal forcing
 // at t_{k+1/2} or null.  r: local residual (nc x nf), overwritten.
+// floors (nullable): incremented once per Gauss point whose tau_m radicand is
+// raised to 4/dt^2 (the reading of an unbounded radicand, see the header).
 template <class T>
 void element_residual(const Mesh& m, const Params& P, int64_t e, const T* un, const T* uo,
-                      const double* f, T* r) {
+                      const double* f, T* r, int64_t* floors = nullptr) {
   const int dim = m.dim, nc = m.nc, nf = m.nf;
   const int IP = dim, IPHI = dim + 1, IMU = dim + 2;
   double h[3];
@@ -356,7 +362,10 @@ void element_residual(const Mesh& m, const Params& P, int64_t e, const T* un, co
     for (int i = 0; i < dim; ++i) { vGv += vt[i] * T(G[i]) * vt[i]; vGJ += vt[i] * T(G[i]) * J[i]; }
     T visc = eta / (rho * T(P.Re));
     T rad = T(4.0 / (dt * dt)) + vGv + vGJ / (rho * T(P.Pe)) + T(P.C_I) * visc * visc * T(GG);
-    if (val(rad) < 4.0 / (dt * dt)) rad = T(4.0 / (dt * dt));
+    if (val(rad) < 4.0 / (dt * dt)) {
+      rad = T(4.0 / (dt * dt));
+      if (floors) ++*floors;
+    }
     T tau_m = T(1.0) / sqrt(rad);
     T tau_c = T(1.0) / (T(trG) * tau_m);
 
@@ -613,6 +622,75 @@ int64_t oracle_jacobian_coo(void* h, const double* prm, const double* Un, const 
       ++cnt;
     }
   return cnt;
+}
+
+// Number of Gauss points (over all leaves) whose tau_m radicand is raised to
+// 4/dt^2, evaluated as in oracle_residual (double precision).
+int64_t oracle_tau_floor_count(void* h, const double* prm, const double* Un, const double* Uo) {
+  Mesh& m = *(Mesh*)h;
+  Params P = unpack(prm);
+  const int L = m.nc * m.nf;
+  std::vector<double> un(L), uo(L), r(L);
+  int64_t floors = 0;
+  for (int64_t e = 0; e < m.n_elem; ++e) {
+    gather<double>(m, e, Un, nullptr, un.data());
+    gather<double>(m, e, Uo, nullptr, uo.data());
+    element_residual<double>(m, P, e, un.data(), uo.data(), nullptr, r.data(), &floors);
+  }
+  return floors;
+}
+
+// oracle_jacvec on several host threads (the CPU baseline on all cores): the
+// same element routine, elements grouped by a greedy colouring in element
+// order so that elements of one colour write disjoint rows; the colours run
+// one after another, the elements of a colour are split among the threads.
+// Within a row the contributions arrive in colour order instead of element
+// order, so results agree with oracle_jacvec to rounding.
+void oracle_jacvec_threads(void* h, const double* prm, const double* Un, const double* Uo, const double* w,
+                           double* y, int n_threads) {
+  Mesh& m = *(Mesh*)h;
+  Params P = unpack(prm);
+  const int L = m.nc * m.nf;
+  if (m.colour_elems.empty()) {
+    std::vector<std::vector<int64_t>> node_elems(m.n_nodes);
+    for (int64_t e = 0; e < m.n_elem; ++e)
+      for (int64_t t = m.P_start[e * m.nc]; t < m.P_start[(e + 1) * m.nc]; ++t) node_elems[m.P_node[t]].push_back(e);
+    std::vector<int> col(m.n_elem, -1);
+    std::vector<int64_t> seen(1024, -1);
+    for (int64_t e = 0; e < m.n_elem; ++e) {
+      for (int64_t t = m.P_start[e * m.nc]; t < m.P_start[(e + 1) * m.nc]; ++t)
+        for (int64_t o : node_elems[m.P_node[t]])
+          if (col[o] >= 0) seen[col[o]] = e;
+      int c = 0;
+      while (c < (int)seen.size() && seen[c] == e) ++c;
+      if (c == (int)seen.size()) seen.push_back(-1);
+      col[e] = c;
+      if ((int)m.colour_elems.size() <= c) m.colour_elems.resize(c + 1);
+      m.colour_elems[c].push_back(e);
+    }
+  }
+  std::fill(y, y + m.n_nodes * m.nf, 0.0);
+  if (n_threads < 1) n_threads = 1;
+  for (const auto& elems : m.colour_elems) {
+    auto work = [&](int tid) {
+      std::vector<Dual> un(L), uo(L), r(L);
+      std::vector<double> rd(L);
+      const int64_t n = (int64_t)elems.size();
+      for (int64_t k = n * tid / n_threads; k < n * (tid + 1) / n_threads; ++k) {
+        const int64_t e = elems[k];
+        gather<Dual>(m, e, Un, w, un.data());
+        gather<Dual>(m, e, Uo, nullptr, uo.data());
+        element_residual<Dual>(m, P, e, un.data(), uo.data(), nullptr, r.data());
+        for (int i = 0; i < L; ++i) rd[i] = r[i].d;
+        scatter(m, e, rd.data(), y);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < n_threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+  }
+  for_constrained_rows(m, [&](int64_t row) { y[row] = w[row]; });
 }
 
 // Diagnostics with the same 2^d Gauss rule: out[0] energy (Eq. energy_functional,

@@ -32,7 +32,7 @@ _lib = None
 
 def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", _LIB_PATH, _SRC]
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", _LIB_PATH, _SRC]
         subprocess.check_call(cmd)
     return _LIB_PATH
 
@@ -55,6 +55,9 @@ def lib():
         L.oracle_jacobian_coo.restype = i64
         L.oracle_jacobian_coo.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.oracle_energy_mass.argtypes = [vp, vp, vp, vp]
+        L.oracle_tau_floor_count.restype = i64
+        L.oracle_tau_floor_count.argtypes = [vp, vp, vp, vp]
+        L.oracle_jacvec_threads.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         _lib = L
     return _lib
 
@@ -140,6 +143,19 @@ class OracleMesh:
         y = np.zeros(self.n_dof)
         lib().oracle_jacvec(self._h, _p(prm), _p(Un), _p(Uo), _p(w), _p(y))
         return y
+
+    def jacvec_threads(self, params, Un, Uo, w, n_threads: int) -> np.ndarray:
+        """jacvec on ``n_threads`` host threads (elements grouped by colour)."""
+        prm = _params_array(params)
+        Un, Uo, w = _vec(Un), _vec(Uo), _vec(w)
+        y = np.zeros(self.n_dof)
+        lib().oracle_jacvec_threads(self._h, _p(prm), _p(Un), _p(Uo), _p(w), _p(y), int(n_threads))
+        return y
+
+    def tau_floor_count(self, params, Un, Uo) -> int:
+        """Gauss points whose tau_m radicand is raised to 4/dt^2."""
+        prm = _params_array(params)
+        return int(lib().oracle_tau_floor_count(self._h, _p(prm), _p(_vec(Un)), _p(_vec(Uo))))
 
     def jacobian(self, params, Un, Uo):
         import scipy.sparse as sp

@@ -1,4 +1,5 @@
-"""Build libchns.so in-tree for sm_103a (nvcc, one -gencode, parallel TUs)."""
+"""Build libchns.so (and the benchmark's libchns_peak.so) in-tree for sm_103a
+(nvcc, one -gencode, parallel TUs)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -10,7 +11,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchns.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["mesh.cpp", "element.cu", "vector.cu", "coarse.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["mesh.cpp", "element.cu", "vector.cu", "coarse.cu", "api.cu", "noalloc.cu", "multigrid.cu", "peak.cu"]
+# the FMA-peak measurement of the benchmark's roofline: a library of its own
+PEAK_SOURCES = ["peak.cu"]
+PEAK_OUT = os.path.join(HERE, "libchns_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -22,7 +26,7 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(OUT):
+    if not os.path.exists(OUT) or not os.path.exists(PEAK_OUT):
         return True
     t = os.path.getmtime(OUT)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
@@ -53,12 +57,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for _, log in results:
             print(log)
-    tmp = OUT + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, OUT)
+    libs = [(OUT, [o for s_, (o, _) in zip(SOURCES, results) if s_ not in PEAK_SOURCES]),
+            (PEAK_OUT, [o for s_, (o, _) in zip(SOURCES, results) if s_ in PEAK_SOURCES])]
+    for out, objs in libs:
+        tmp = out + ".tmp"
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, out)
     return OUT
 
 

@@ -17,14 +17,25 @@ LIB_PATH = os.path.join(_HERE, "libchns.so")
 
 CHNS_FP64 = 0
 CHNS_FP32_BULK = 1
+CHNS_PC_TWO_LEVEL = 0
+CHNS_PC_MULTIGRID = 1
+# FP32 J.w schedules the autotuner chooses among (StepStats.jacvec_variant)
+JACVEC_VARIANTS = ["element-local buffer + node gather, 128-thread blocks, 6/SM",
+                   "element-local buffer + node gather, 256-thread blocks, 3/SM",
+                   "element-local buffer + node gather, 64-thread blocks, 12/SM",
+                   "element-local buffer + node gather, 128-thread blocks, 8/SM (64 registers)",
+                   "element colours, in-place adds into y, 128-thread blocks",
+                   "element-local buffer + node gather, 128-thread blocks, 5/SM (102 registers)",
+                   "element-local buffer + node gather, 128-thread blocks, 4/SM (128 registers)"]
 STATUS = {0: "CHNS_OK", 1: "CHNS_ERR_ARG", 2: "CHNS_ERR_MESH", 3: "CHNS_ERR_CUDA",
           4: "CHNS_ERR_NONFINITE", 5: "CHNS_ERR_NEWTON", 6: "CHNS_ERR_KRYLOV",
-          7: "CHNS_ERR_TIMEOUT", 8: "CHNS_ERR_OOM"}
+          8: "CHNS_ERR_OOM"}
 
 EXPORTS = ["chns_mesh_create", "chns_mesh_info", "chns_mesh_node_coords", "chns_mesh_destroy",
            "chns_residual", "chns_jacvec", "chns_init_mu", "chns_step", "chns_energy_mass",
            "chns_batch_create", "chns_batch_step", "chns_batch_destroy", "chns_last_error",
-           "chns_kernel_launches", "chns_energy_mass_noalloc"]
+           "chns_kernel_launches", "chns_energy_mass_noalloc", "chns_tau_floor_count",
+           "chns_mesh_check", "chns_mesh_jacvec_schedule"]
 
 
 class ChnsError(RuntimeError):
@@ -51,15 +62,22 @@ class SolverOpts(ctypes.Structure):
                 ("newton_max_it", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_max_it", ctypes.c_int),
                 ("precision", ctypes.c_int), ("reuse_preconditioner", ctypes.c_int),
-                ("coarse_level", ctypes.c_int)]
+                ("coarse_level", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("preconditioner", ctypes.c_int), ("mg_coarsest", ctypes.c_int), ("mg_smooth", ctypes.c_int),
+                ("mg_omega", ctypes.c_double), ("block_iteration", ctypes.c_int), ("block_tol", ctypes.c_double),
+                ("block_max_it", ctypes.c_int), ("autotune", ctypes.c_int)]
 
     @classmethod
     def make(cls, precision="fp64", newton_rtol=1e-10, newton_atol=1e-13, newton_max_it=20,
              krylov_rtol=1e-4, krylov_restart=64, krylov_max_it=600, reuse_preconditioner=1,
-             coarse_level=-1):
+             coarse_level=-1, use_graph=True, preconditioner="two_level", mg_coarsest=-1, mg_smooth=1,
+             mg_omega=0.7, block_iteration=False, block_tol=1e-4, block_max_it=50, autotune=False):
         prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
+        pcn = {"two_level": CHNS_PC_TWO_LEVEL, "multigrid": CHNS_PC_MULTIGRID}[preconditioner]
         return cls(newton_rtol, newton_atol, newton_max_it, krylov_rtol, krylov_restart, krylov_max_it,
-                   prec, int(reuse_preconditioner), int(coarse_level))
+                   prec, int(reuse_preconditioner), int(coarse_level), int(bool(use_graph)), pcn,
+                   int(mg_coarsest), int(mg_smooth), float(mg_omega), int(bool(block_iteration)),
+                   float(block_tol), int(block_max_it), int(bool(autotune)))
 
 
 class StepStats(ctypes.Structure):
@@ -70,7 +88,7 @@ class StepStats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("jacvec_ms", ctypes.c_double),
                 ("jacvec_calls", ctypes.c_int), ("residual_ms", ctypes.c_double),
                 ("residual_calls", ctypes.c_int), ("precond_ms", ctypes.c_double),
-                ("fp64_newton_its", ctypes.c_int)]
+                ("fp64_newton_its", ctypes.c_int), ("block_its", ctypes.c_int), ("jacvec_variant", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +125,12 @@ def lib():
         L.chns_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.chns_energy_mass.restype = st
         L.chns_energy_mass.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.chns_tau_floor_count.restype = st
+        L.chns_tau_floor_count.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.chns_mesh_check.restype = st
+        L.chns_mesh_check.argtypes = [vp]
+        L.chns_mesh_jacvec_schedule.restype = st
+        L.chns_mesh_jacvec_schedule.argtypes = [vp, i32, vp, vp]
         L.chns_energy_mass_noalloc.restype = st
         L.chns_energy_mass_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.chns_batch_create.restype = st
@@ -169,6 +193,17 @@ class Mesh:
     def handle(self):
         return self._h
 
+    def jacvec_schedule(self, variant: int = -1):
+        """Fix (variant >= 0) or read the FP32 J.w schedule; returns (current, times_ms)."""
+        cur = ctypes.c_int()
+        times = (ctypes.c_double * 7)()
+        _check(lib().chns_mesh_jacvec_schedule(self._h, int(variant), ctypes.byref(cur), times))
+        return cur.value, list(times)
+
+    def check(self):
+        """Host-side validation of colouring, gather lists and hanging constraints."""
+        _check(lib().chns_mesh_check(self._h))
+
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.chns_mesh_destroy(self._h)
@@ -228,6 +263,14 @@ def energy_mass(mesh: Mesh, params, U, stream=None):
     _check(lib().chns_energy_mass(mesh.handle, ctypes.byref(prm), _ptr(U), ctypes.byref(e), ctypes.byref(m),
                                   ctypes.byref(b), _stream(stream)))
     return e.value, m.value, b.value
+
+
+def tau_floor_count(mesh: Mesh, params, U_new, U_old, stream=None) -> int:
+    prm = Params.of(params)
+    c = ctypes.c_int64()
+    _check(lib().chns_tau_floor_count(mesh.handle, ctypes.byref(prm), _ptr(U_new), _ptr(U_old), ctypes.byref(c),
+                                      _stream(stream)))
+    return int(c.value)
 
 
 def kernel_launches() -> int:

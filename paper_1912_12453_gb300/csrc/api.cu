@@ -1,5 +1,6 @@
 // C ABI of libchns: meshes, operator applies, the Newton-Krylov CN step
 // (Sec. 3.5), diagnostics and batches.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -11,21 +12,20 @@
 #include "coarse.h"
 #include "kernels.h"
 #include "vector.h"
+#include "solver.h"
+#include "multigrid.h"
 
 namespace chns {
 chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor, int max_level,
                        const double lo[3], const double hi[3], chns_mesh *m);
 chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u);
 chns_status build_gather(chns_mesh *m);
+chns_status validate_mesh(const chns_mesh *m);
 const char *last_error();
 uint64_t launches();
 }  // namespace chns
 
 using namespace chns;
-
-namespace {
-
-inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
 #define TRY(expr)                               \
   do {                                          \
@@ -33,15 +33,7 @@ inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
     if (s_ != CHNS_OK) return s_;               \
   } while (0)
 
-chns_status check_launch() {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_error("kernel launch failed: %s", cudaGetErrorString(e));
-    return CHNS_ERR_CUDA;
-  }
-  return CHNS_OK;
-}
-
+namespace chns {
 chns_status check_params(const chns_mesh *m, const chns_params *p) {
   if (!m || !p) { set_error("null mesh or params"); return CHNS_ERR_ARG; }
   if (p->dim != m->dim) { set_error("params.dim %d != mesh dim %d", p->dim, m->dim); return CHNS_ERR_ARG; }
@@ -49,6 +41,15 @@ chns_status check_params(const chns_mesh *m, const chns_params *p) {
       !(p->rho_ratio > 0) || !(p->eta_ratio > 0) || !(p->C_I >= 0)) {
     set_error("parameters must be positive");
     return CHNS_ERR_ARG;
+  }
+  return CHNS_OK;
+}
+
+chns_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("kernel launch failed: %s", cudaGetErrorString(e));
+    return CHNS_ERR_CUDA;
   }
   return CHNS_OK;
 }
@@ -93,6 +94,103 @@ chns_status jacvec_prepared(chns_mesh *m, const PhysCoef &pc, const T *ut, const
   launch_jacvec<T>(m, pc, ut, dl, w, E, y, st);
   return check_launch();
 }
+template chns_status prepare<float>(chns_mesh *, const double *, const double *, cudaStream_t, float **, float **);
+template chns_status prepare<double>(chns_mesh *, const double *, const double *, cudaStream_t, double **, double **);
+template chns_status ensure_ebuf<float>(chns_mesh *, float **);
+template chns_status ensure_ebuf<double>(chns_mesh *, double **);
+template chns_status jacvec_prepared<float>(chns_mesh *, const PhysCoef &, const float *, const float *, const float *,
+                                            float *, cudaStream_t);
+template chns_status jacvec_prepared<double>(chns_mesh *, const PhysCoef &, const double *, const double *,
+                                             const double *, double *, cudaStream_t);
+
+// ---------------------------------------------------------------- block-Jacobi by probing
+// The nodal (nf x nf) diagonal blocks of J are read off J applied to the
+// indicator of one field on the nodes of one node colour: nodes of a colour
+// never share an element, so each probed node sees only its own block.
+template <typename T>
+chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, DevBuf &out,
+                               cudaStream_t st, double scale) {
+  Workspace &ws = m->ws;
+  const int nf = m->nf;
+  const int64_t n = m->n_nodes * nf;
+  TRY(out.ensure(sizeof(T) * m->n_nodes * nf * nf + 16));
+  TRY(ws.wv.ensure(sizeof(T) * n));
+  TRY(ws.yv.ensure(sizeof(T) * n));
+  T *w = ws.wv.as<T>(), *y = ws.yv.as<T>(), *B = out.as<T>();
+  for (int c = 0; c < m->n_node_colours; ++c) {
+    int64_t b = m->node_colour_start[c], e = m->node_colour_start[c + 1];
+    for (int f = 0; f < nf; ++f) {
+      CHNS_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(T) * n, st));
+      probe_set<T>(m->node_perm + b, e - b, nf, f, w, st);
+      TRY(jacvec_prepared<T>(m, pc, ut, dl, w, y, st));
+      probe_get<T>(m->node_perm + b, e - b, nf, f, y, B, st);
+    }
+  }
+  int *bad = reinterpret_cast<int *>(reinterpret_cast<char *>(B) + sizeof(T) * m->n_nodes * nf * nf);
+  CHNS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  invert_blocks<T>(B, m->n_nodes, nf, bad, scale, st);
+  int hbad = 0;
+  CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hbad) { set_error("singular nodal diagonal block in the preconditioner"); return CHNS_ERR_KRYLOV; }
+  return check_launch();
+}
+template chns_status build_block_jacobi<float>(chns_mesh *, const PhysCoef &, const float *, const float *, DevBuf &,
+                                              cudaStream_t, double);
+template chns_status build_block_jacobi<double>(chns_mesh *, const PhysCoef &, const double *, const double *, DevBuf &,
+                                               cudaStream_t, double);
+
+
+
+// Autotuner of the FP32 J.w schedule of a mesh: every schedule of
+// launch_jacvec is timed with CUDA events on the launching stream (one
+// warm-up, then the median of five applies to the prepared state) and the
+// fastest is kept for the mesh's later FP32 applies.  Runs once per mesh.
+chns_status autotune_jacvec(chns_mesh *m, const PhysCoef &pc, const float *ut, const float *dl, cudaStream_t st) {
+  if (m->jv_tuned) return CHNS_OK;
+  const int64_t n = m->n_nodes * m->nf;
+  DevBuf w, y;
+  TRY(w.ensure(sizeof(float) * n + 16));
+  TRY(y.ensure(sizeof(float) * n + 16));
+  float *E = nullptr;
+  TRY(ensure_ebuf<float>(m, &E));
+  CHNS_CUDA_TRY(cudaMemcpyAsync(w.as<float>(), ut, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+  cudaEvent_t e[2];
+  CHNS_CUDA_TRY(cudaEventCreate(&e[0]));
+  CHNS_CUDA_TRY(cudaEventCreate(&e[1]));
+  int best = 0;
+  double tbest = 1e300;
+  for (int v = 0; v < kJacvecVariants; ++v) {
+    launch_jacvec<float>(m, pc, ut, dl, w.as<float>(), E, y.as<float>(), st, v);
+    std::vector<float> ts;
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e[0], st);
+      launch_jacvec<float>(m, pc, ut, dl, w.as<float>(), E, y.as<float>(), st, v);
+      cudaEventRecord(e[1], st);
+      cudaEventSynchronize(e[1]);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e[0], e[1]);
+      ts.push_back(t);
+    }
+    std::sort(ts.begin(), ts.end());
+    m->jv_times[v] = ts[2];
+    if (ts[2] < tbest) { tbest = ts[2]; best = v; }
+  }
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  w.release();
+  y.release();
+  TRY(check_launch());
+  m->jv_variant = best;
+  m->jv_tuned = true;
+  return CHNS_OK;
+}
+}  // namespace chns
+
+namespace {
+
+inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
 
 chns_status ensure_events(Workspace &ws, size_t n) {
   while (ws.ev.size() < n) {
@@ -180,55 +278,19 @@ struct Timer {
   }
 };
 
-// ---------------------------------------------------------------- block-Jacobi by probing
-// The nodal (nf x nf) diagonal blocks of J are read off J applied to the
-// indicator of one field on the nodes of one node colour: nodes of a colour
-// never share an element, so each probed node sees only its own block.
-template <typename T>
-chns_status build_block_jacobi(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, DevBuf &out,
-                               cudaStream_t st) {
-  Workspace &ws = m->ws;
-  const int nf = m->nf;
-  const int64_t n = m->n_nodes * nf;
-  TRY(out.ensure(sizeof(T) * m->n_nodes * nf * nf + 16));
-  TRY(ws.wv.ensure(sizeof(T) * n));
-  TRY(ws.yv.ensure(sizeof(T) * n));
-  T *w = ws.wv.as<T>(), *y = ws.yv.as<T>(), *B = out.as<T>();
-  for (int c = 0; c < m->n_node_colours; ++c) {
-    int64_t b = m->node_colour_start[c], e = m->node_colour_start[c + 1];
-    for (int f = 0; f < nf; ++f) {
-      CHNS_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(T) * n, st));
-      probe_set<T>(m->node_perm + b, e - b, nf, f, w, st);
-      TRY(jacvec_prepared<T>(m, pc, ut, dl, w, y, st));
-      probe_get<T>(m->node_perm + b, e - b, nf, f, y, B, st);
-    }
-  }
-  int *bad = reinterpret_cast<int *>(reinterpret_cast<char *>(B) + sizeof(T) * m->n_nodes * nf * nf);
-  CHNS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  invert_blocks<T>(B, m->n_nodes, nf, bad, st);
-  int hbad = 0;
-  CHNS_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hbad) { set_error("singular nodal diagonal block in the preconditioner"); return CHNS_ERR_KRYLOV; }
-  return check_launch();
-}
-
 // What an Arnoldi-step graph bakes in: buffers, sizes, coarse-space state and
 // the element coefficients (kernel arguments by value)
 struct StepKey {
-  const void *p[15];
-  int64_t i[5];
+  const void *p[16];
+  int64_t i[8];
   PhysCoef pc;
 };
 
-// CHNS_NO_GRAPHS=1 launches the Arnoldi steps kernel by kernel
-bool use_graphs() {
-  static int on = -1;
-  if (on < 0) {
-    const char *e = std::getenv("CHNS_NO_GRAPHS");
-    on = (e && *e && *e != '0') ? 0 : 1;
-  }
-  return on == 1;
+// CHNS_INJECT=krylov: the next FGMRES reports a breakdown (host-side fault
+// injection; read at every solve so a test can set and clear it)
+bool inject_krylov_fault() {
+  const char *e = std::getenv("CHNS_INJECT");
+  return e && std::strcmp(e, "krylov") == 0;
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -245,7 +307,7 @@ bool use_graphs() {
 // the queued step j + 1 is discarded.
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
-                   const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
+                   bool mg, const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
                    cudaStream_t st) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
@@ -291,7 +353,8 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     double *h1 = hd + 3 * K * sl, *h2 = h1 + K, *nr = h1 + 2 * K;
     T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
     T *zj = Z + (int64_t)j * ld;
-    precond_apply<T>(m, Binv, coarse, vj, zj, s);
+    if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
+    else precond_apply<T>(m, Binv, coarse, vj, zj, s);
     int ev = 0;
     if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j], s, cudaEventRecordExternal));
     else TRY(tj.begin(s, &ev));
@@ -308,7 +371,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   // Arnoldi steps as CUDA graphs (one per j, captured at first use): a step
   // is ~25 launches of mostly short kernels, and host launch cost, not the
   // GPU, bounds a step launched one kernel at a time
-  const bool graphs = use_graphs();
+  const bool graphs = o.use_graph != 0;
   T *Ebuf = nullptr;
   TRY(ensure_ebuf<T>(m, &Ebuf));
   if (graphs) {
@@ -318,8 +381,9 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     key.p[6] = hd; key.p[7] = ws.hpinned; key.p[8] = m->coarse.vec.as<void>();
     key.p[9] = m->coarse.rpart.as<void>(); key.p[10] = m->coarse.M.as<void>();
     key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
-    key.p[14] = ctr;
+    key.p[14] = ctr; key.p[15] = mg ? m->mg : nullptr;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
+    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph; key.i[7] = m->jv_variant;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
     if (G.key.size() != sizeof(key) || std::memcmp(G.key.data(), kb, sizeof(key)) != 0) {
@@ -408,7 +472,11 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
       }
       double a = H[j * mr + j], c = H[(j + 1) * mr + j];
       double rr = std::hypot(a, c);
-      if (rr == 0.0) { set_error("FGMRES breakdown"); return CHNS_ERR_KRYLOV; }
+      if (rr == 0.0 || inject_krylov_fault()) {
+        CHNS_CUDA_TRY(cudaStreamSynchronize(st));  // the queued step j + 1 has finished
+        set_error("FGMRES breakdown at iteration %d", total + 1);
+        return CHNS_ERR_KRYLOV;
+      }
       cs[j] = a / rr;
       sn[j] = c / rr;
       H[j * mr + j] = rr;
@@ -502,20 +570,29 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   double *F = ws.F.as<double>(), *dU = ws.dU.as<double>();
   Timer tj, tr, tp;  // accumulated J.w, residual and preconditioner times
   const bool mixed = o.precision == CHNS_FP32_BULK;
-  bool use64 = !mixed;
+  const bool use_mg = o.preconditioner == CHNS_PC_MULTIGRID;
   int Lc = o.coarse_level;
   if (Lc < 0) Lc = std::min(3, m->min_level - 1);
-  const bool coarse = Lc >= 1;
+  const bool coarse = !use_mg && Lc >= 1;
   if (coarse) TRY(coarse_setup(m, Lc));
+  if (use_mg) {
+    TRY(mg_setup(m, o.mg_coarsest > 0 ? o.mg_coarsest : (m->dim == 3 ? 2 : 3)));
+    Lc = m->mg->bottom_level;
+    m->mg->autotune = o.autotune != 0;
+  }
   // a preconditioner from an earlier step is reused while it is young enough
-  // and was built for the same precision, parameters and coarse space
+  // and was built for the same precision, parameters and preconditioner
   bool have_pc = ws.pc_steps_left > 0 && ws.pc_precision == (int)o.precision && ws.pc_coarse == Lc &&
-                 std::memcmp(&ws.pc_params, p, sizeof(chns_params)) == 0 && o.reuse_preconditioner > 0;
+                 ws.pc_kind == (int)o.preconditioner && ws.pc_smooth == o.mg_smooth && ws.pc_omega == o.mg_omega &&
+                 std::memcmp(&ws.pc_params, p, sizeof(chns_params)) == 0 && o.reuse_preconditioner > 0 &&
+                 (!use_mg || m->mg->ready);
   if (have_pc) --ws.pc_steps_left;
-  bool have_pc64 = false;
   auto mark_built = [&]() {
     ws.pc_precision = (int)o.precision;
     ws.pc_coarse = Lc;
+    ws.pc_kind = (int)o.preconditioner;
+    ws.pc_smooth = o.mg_smooth;
+    ws.pc_omega = o.mg_omega;
     ws.pc_params = *p;
     ws.pc_steps_left = o.reuse_preconditioner > 0 ? o.reuse_preconditioner - 1 : 0;
   };
@@ -523,11 +600,16 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   if (Unm1) vec_lincomb(2.0, Un, -1.0, Unm1, U, n, st);
   else CHNS_CUDA_TRY(cudaMemcpyAsync(U, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
 
+  // fields solved for: all (coupled Newton), or one block of the NS <-> CH
+  // block iteration (Sec. 3.1, Fig. flowchart_block); the other block's rows
+  // are identity rows of J.w and zero rows of the residual
+  uint32_t fmask = 0xffu;
   double *ut = nullptr, *dl = nullptr;
   auto residual = [&](double *fn) -> chns_status {
     TRY(prepare<double>(m, U, Un, st, &ut, &dl));
     if (stats) { TRY(ensure_events(ws, 64)); CHNS_CUDA_TRY(cudaEventRecord(ws.ev[60], st)); }
     TRY(residual_prepared(m, pc, U, ut, dl, forcing, bc, F, st));
+    if (fmask != 0xffu) vec_mask_fields(F, m->n_nodes, nf, fmask, st);
     if (stats) CHNS_CUDA_TRY(cudaEventRecord(ws.ev[61], st));
     TRY(norm2(m, F, fn, st));
     if (stats) {
@@ -539,9 +621,6 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     if (!std::isfinite(*fn)) { set_error("non-finite residual norm"); return CHNS_ERR_NONFINITE; }
     return CHNS_OK;
   };
-  double fn = 0.0;
-  TRY(residual(&fn));
-  const double f0 = fn;
   // batched meshes: every instance must meet its own tolerance; converged
   // instances get a zero right-hand side (their correction is then exactly
   // zero: the operator and the preconditioner are block diagonal)
@@ -562,93 +641,175 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     for (int q = 0; q < ni; ++q) fi[q] = std::sqrt(h[q]);
     return CHNS_OK;
   };
-  TRY(instance_norms());
-  fi0 = fi;
-  auto converged = [&]() {
-    if (ni == 1) return fn <= std::max(o.newton_rtol * f0, o.newton_atol);
-    for (int q = 0; q < ni; ++q)
-      if (!(fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol))) return false;
-    return true;
-  };
   int its = 0, kits = 0, its64 = 0;
-  while (!converged()) {
-    if (ni > 1)
+  double f0_all = -1.0, fn_last = 0.0;
+
+  // Newton on the fields of fmask from the current U, to newton_rtol of its
+  // own initial residual (Sec. 3.5)
+  auto solve = [&](uint32_t mask) -> chns_status {
+    fmask = mask;
+    PhysCoef pcs = pc;
+    pcs.fmask = mask;
+    bool use64 = !mixed;
+    bool have_pc64 = false;
+    if (mask != 0xffu) have_pc = false;  // the operator differs per block: build for each sub-solve
+    double fn = 0.0;
+    TRY(residual(&fn));
+    const double f0 = fn;
+    if (f0_all < 0.0) f0_all = f0;
+    TRY(instance_norms());
+    fi0 = fi;
+    auto converged = [&]() {
+      if (ni == 1) return fn <= std::max(o.newton_rtol * f0, o.newton_atol);
       for (int q = 0; q < ni; ++q)
-        if (fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol)) {
-          const int64_t a = m->inst_node_start[q] * nf, b = m->inst_node_start[q + 1] * nf;
-          CHNS_CUDA_TRY(cudaMemsetAsync(F + a, 0, sizeof(double) * (b - a), st));
+        if (!(fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol))) return false;
+      return true;
+    };
+    int sub_its = 0;
+    while (!converged()) {
+      if (ni > 1)
+        for (int q = 0; q < ni; ++q)
+          if (fi[q] <= std::max(o.newton_rtol * fi0[q], o.newton_atol)) {
+            const int64_t a = m->inst_node_start[q] * nf, b = m->inst_node_start[q + 1] * nf;
+            CHNS_CUDA_TRY(cudaMemsetAsync(F + a, 0, sizeof(double) * (b - a), st));
+          }
+      if (sub_its >= o.newton_max_it) {
+        ws.pc_steps_left = 0;
+        set_error("Newton reached %d iterations with ||F|| = %.3e (start %.3e)", sub_its, fn, f0);
+        if (stats) { stats->newton_its = its; stats->res_final = fn; stats->res0 = f0; }
+        return CHNS_ERR_NEWTON;
+      }
+      int k = 0;
+      Timer tk;  // event slots 0.. (the residual uses slots 60, 61)
+      tk.ws = &ws;
+      tk.on = stats != nullptr;
+      // forcing term: never ask the linear solve for more than the Newton
+      // target needs (with a factor-2 margin), never less than krylov_rtol
+      chns_solver_opts oi = o;
+      const double target = std::max(o.newton_rtol * f0, o.newton_atol);
+      oi.krylov_rtol = std::max(o.krylov_rtol, std::min(0.5, 0.5 * target / fn));
+      vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
+      auto a = std::chrono::steady_clock::now();
+      if (!use64) {
+        float *ut_t = nullptr, *dl_t = nullptr;
+        TRY(prepare<float>(m, U, Un, st, &ut_t, &dl_t));
+        if (o.autotune && !m->jv_tuned) TRY(autotune_jacvec(m, pcs, ut_t, dl_t, st));
+        if (!have_pc || !o.reuse_preconditioner || (use_mg && m->mg->elem_size != (int)sizeof(float))) {
+          if (use_mg) {
+            TRY(mg_build<float>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
+          } else {
+            TRY(build_block_jacobi<float>(m, pcs, ut_t, dl_t, ws.binv, st, 1.0));
+            if (coarse) TRY(build_coarse_operator<float>(m, pcs, ut_t, dl_t, st));
+          }
+          have_pc = true;
+          mark_built();
+          tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+        } else if (use_mg) {
+          TRY(mg_update_state<float>(m, ut_t, dl_t, st));  // coarse levels follow the Newton iterate
         }
-    if (its >= o.newton_max_it) {
-      ws.pc_steps_left = 0;
-      set_error("Newton reached %d iterations with ||F|| = %.3e (start %.3e)", its, fn, f0);
-      if (stats) { stats->newton_its = its; stats->res_final = fn; stats->res0 = f0; }
+        TRY(fgmres<float>(m, pcs, ut_t, dl_t, ws.binv.as<float>(), coarse, use_mg, F, dU, oi, &k, tk, st));
+      } else {
+        double *ut_t = nullptr, *dl_t = nullptr;
+        TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
+        if (mixed) {
+          if (use_mg) {  // the FP64 finish rebuilds the hierarchy's operators in double once
+            if (!have_pc64) {
+              TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
+              have_pc64 = true;
+              tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+            } else {
+              TRY(mg_update_state<double>(m, ut_t, dl_t, st));
+            }
+          } else if (!have_pc64) {  // promote the FP32 blocks (built by an earlier FP32 iteration or step)
+            TRY(ws.binv64.ensure(sizeof(double) * nb));
+            vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
+            have_pc64 = true;
+          }
+        } else if (!have_pc || !o.reuse_preconditioner || (use_mg && m->mg->elem_size != (int)sizeof(double))) {
+          if (use_mg) {
+            TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
+          } else {
+            TRY(build_block_jacobi<double>(m, pcs, ut_t, dl_t, ws.binv64, st, 1.0));
+            if (coarse) TRY(build_coarse_operator<double>(m, pcs, ut_t, dl_t, st));
+          }
+          have_pc = true;
+          mark_built();
+          tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+        } else if (use_mg) {
+          TRY(mg_update_state<double>(m, ut_t, dl_t, st));
+        }
+        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st));
+        if (mixed) ++its64;
+      }
+      tj.ms += tk.ms;
+      tj.calls += tk.calls;
+      kits += k;
+      vec_axpby(1.0, dU, 1.0, U, n, st);
+      ++its;
+      ++sub_its;
+      const double prev = fn;
+      TRY(residual(&fn));
+      TRY(instance_norms());
+      if (trace_on())
+        fprintf(stderr, "[chns] newton %d (fields %#x) |F|/|F0| = %.3e krylov %d (%s J.w)\n", its, mask, fn / f0, k,
+                use64 ? "fp64" : "fp32");
+      if (mixed && !use64 && fn * kFp32MinReduction > prev) use64 = true;
+    }
+    fn_last = fn;
+    return CHNS_OK;
+  };
+
+  int blocks = 0;
+  if (!o.block_iteration) {
+    TRY(solve(0xffu));
+  } else {
+    const int d = m->dim;
+    const uint32_t ns = (1u << (d + 1)) - 1u;            // v_1..v_d, p
+    const uint32_t ch = (1u << (d + 1)) | (1u << (d + 2));  // phi, mu
+    TRY(ws.Ublk.ensure(sizeof(double) * n));
+    double *Uprev = ws.Ublk.as<double>();
+    TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+    TRY(ws.hdev.ensure(sizeof(double) * 8 * kHessSlot));
+    TRY(ensure_pinned(ws));
+    bool done = false;
+    for (int l = 0; l < o.block_max_it && !done; ++l) {
+      CHNS_CUDA_TRY(cudaMemcpyAsync(Uprev, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      TRY(solve(ns));
+      TRY(solve(ch));
+      ++blocks;
+      // stop once a block iteration after the first changes no entry of
+      // (v, p, phi, mu) by more than block_tol
+      vec_maxabs_diff(U, Uprev, n, ws.red.as<double>(), ws.hdev.as<double>(), st);
+      CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, ws.hdev.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, st));
+      CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+      const double change = ws.hpinned[0];
+      if (trace_on()) fprintf(stderr, "[chns] block iteration %d max|dU| = %.3e\n", l, change);
+      if (!std::isfinite(change)) { set_error("non-finite block iteration change"); return CHNS_ERR_NONFINITE; }
+      if (l >= 1 && change <= o.block_tol) done = true;
+    }
+    ws.pc_steps_left = 0;  // the last build was for one block only
+    if (!done) {
+      set_error("block iteration did not reach block_tol %.3e in %d iterations", o.block_tol, o.block_max_it);
+      if (stats) { stats->newton_its = its; stats->block_its = blocks; }
       return CHNS_ERR_NEWTON;
     }
-    int k = 0;
-    Timer tk;  // event slots 0.. (the residual uses slots 60, 61)
-    tk.ws = &ws;
-    tk.on = stats != nullptr;
-    // forcing term: never ask the linear solve for more than the Newton
-    // target needs (with a factor-2 margin), never less than krylov_rtol
-    chns_solver_opts oi = o;
-    const double target = std::max(o.newton_rtol * f0, o.newton_atol);
-    oi.krylov_rtol = std::max(o.krylov_rtol, std::min(0.5, 0.5 * target / fn));
-    vec_axpby(-1.0, F, 0.0, F, n, st);  // b = -F
-    auto a = std::chrono::steady_clock::now();
-    if (!use64) {
-      float *ut_t = nullptr, *dl_t = nullptr;
-      TRY(prepare<float>(m, U, Un, st, &ut_t, &dl_t));
-      if (!have_pc || !o.reuse_preconditioner) {
-        TRY(build_block_jacobi<float>(m, pc, ut_t, dl_t, ws.binv, st));
-        if (coarse) TRY(build_coarse_operator<float>(m, pc, ut_t, dl_t, st));
-        have_pc = true;
-        mark_built();
-        tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-      }
-      TRY(fgmres<float>(m, pc, ut_t, dl_t, ws.binv.as<float>(), coarse, F, dU, oi, &k, tk, st));
-    } else {
-      double *ut_t = nullptr, *dl_t = nullptr;
-      TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
-      if (mixed) {
-        if (!have_pc64) {  // promote the FP32 blocks (built by an earlier FP32 iteration or step)
-          TRY(ws.binv64.ensure(sizeof(double) * nb));
-          vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
-          have_pc64 = true;
-        }
-      } else if (!have_pc || !o.reuse_preconditioner) {
-        TRY(build_block_jacobi<double>(m, pc, ut_t, dl_t, ws.binv64, st));
-        if (coarse) TRY(build_coarse_operator<double>(m, pc, ut_t, dl_t, st));
-        have_pc = true;
-        mark_built();
-        tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-      }
-      TRY(fgmres<double>(m, pc, ut_t, dl_t, ws.binv64.as<double>(), coarse, F, dU, oi, &k, tk, st));
-      if (mixed) ++its64;
-    }
-    tj.ms += tk.ms;
-    tj.calls += tk.calls;
-    kits += k;
-    vec_axpby(1.0, dU, 1.0, U, n, st);
-    ++its;
-    const double prev = fn;
-    TRY(residual(&fn));
-    TRY(instance_norms());
-    if (trace_on())
-      fprintf(stderr, "[chns] newton %d |F|/|F0| = %.3e krylov %d (%s J.w)\n", its, fn / f0, k,
-              use64 ? "fp64" : "fp32");
-    if (mixed && !use64 && fn * kFp32MinReduction > prev) use64 = true;
+    // coupled residual of the block-iteration result (reported, not used)
+    fmask = 0xffu;
+    TRY(residual(&fn_last));
   }
   if (stats) {
     stats->newton_its = its;
     stats->krylov_its_total = kits;
-    stats->res0 = f0;
-    stats->res_final = fn;
+    stats->res0 = f0_all;
+    stats->res_final = fn_last;
     stats->jacvec_ms = tj.ms;
     stats->jacvec_calls = tj.calls;
     stats->residual_ms = tr.ms;
     stats->residual_calls = tr.calls;
     stats->precond_ms = tp.ms;
     stats->fp64_newton_its = its64;
+    stats->block_its = blocks;
+    stats->jacvec_variant = m->jv_variant;
   }
   return CHNS_OK;
 }
@@ -681,7 +842,12 @@ chns_status step_impl(chns_mesh *m, const chns_params *p, const chns_solver_opts
   if (!o || !U_n || !U_np1) { set_error("null argument"); return CHNS_ERR_ARG; }
   if (U_np1 == U_n) { set_error("U_np1 may not alias U_n"); return CHNS_ERR_ARG; }
   if (o->krylov_restart < 1 || o->krylov_restart > kMaxRestart || o->krylov_max_it < 1 || o->newton_max_it < 0 ||
-      o->coarse_level > 16) {
+      o->coarse_level > 16 || o->use_graph < 0 || o->use_graph > 1 ||
+      (o->preconditioner != CHNS_PC_TWO_LEVEL && o->preconditioner != CHNS_PC_MULTIGRID) ||
+      (o->preconditioner == CHNS_PC_MULTIGRID && (o->mg_smooth < 1 || o->mg_smooth > 8 || !(o->mg_omega > 0.0) ||
+                                                  !(o->mg_omega <= 1.0) || o->mg_coarsest > 16)) ||
+      o->block_iteration < 0 || o->block_iteration > 1 || o->autotune < 0 || o->autotune > 1 ||
+      (o->block_iteration && (!(o->block_tol > 0.0) || o->block_max_it < 1))) {
     set_error("invalid solver options");
     return CHNS_ERR_ARG;
   }
@@ -769,11 +935,13 @@ void chns_mesh_destroy(chns_mesh *m) {
   cudaFree(m->node_inst);
   cudaFree(m->coef32);
   cudaFree(m->coef64);
+  chns::mg_release(m->mg);
+  m->mg = nullptr;
   m->coarse.release();
   m->ws.ut.release(); m->ws.dl.release(); m->ws.ut32.release(); m->ws.dl32.release(); m->ws.f.release();
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
-  m->ws.e32.release(); m->ws.e64.release();
+  m->ws.e32.release(); m->ws.e64.release(); m->ws.ctr.release(); m->ws.count.release();
   delete m;
   cudaSetDevice(prev);
 }
@@ -864,6 +1032,47 @@ chns_status chns_step(const chns_mesh *mc, const chns_params *p, const chns_solv
                       chns_step_stats *stats, void *stream) {
   TRY(check_params(mc, p));
   return step_impl(const_cast<chns_mesh *>(mc), p, o, U_n, U_nm1, forcing, bc, U_np1, stats, S(stream));
+}
+
+chns_status chns_tau_floor_count(const chns_mesh *mc, const chns_params *p, const double *U_new,
+                                 const double *U_old, int64_t *count, void *stream) {
+  TRY(check_params(mc, p));
+  if (!U_new || !U_old || !count) { set_error("null argument"); return CHNS_ERR_ARG; }
+  chns_mesh *m = const_cast<chns_mesh *>(mc);
+  cudaStream_t st = S(stream);
+  double *ut = nullptr, *dl = nullptr;
+  TRY(prepare<double>(m, U_new, U_old, st, &ut, &dl));
+  Workspace &ws = m->ws;
+  TRY(ws.count.ensure(sizeof(unsigned long long)));
+  TRY(ensure_pinned(ws));
+  unsigned long long *cnt = ws.count.as<unsigned long long>();
+  CHNS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  launch_tau_floor_count(m, make_coef(*p, m->lo, m->hi), ut, dl, cnt, st);
+  TRY(check_launch());
+  CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+  unsigned long long v = 0;
+  std::memcpy(&v, ws.hpinned, sizeof(v));
+  *count = (int64_t)v;
+  return CHNS_OK;
+}
+
+chns_status chns_mesh_jacvec_schedule(chns_mesh *m, int variant, int *current, double *times_ms) {
+  if (!m) { set_error("null mesh"); return CHNS_ERR_ARG; }
+  if (variant < -1 || variant >= kJacvecVariants) { set_error("schedule %d out of range", variant); return CHNS_ERR_ARG; }
+  if (variant >= 0) {
+    m->jv_variant = variant;
+    m->jv_tuned = true;
+  }
+  if (current) *current = m->jv_variant;
+  if (times_ms)
+    for (int v = 0; v < kJacvecVariants; ++v) times_ms[v] = m->jv_times[v];
+  return CHNS_OK;
+}
+
+chns_status chns_mesh_check(const chns_mesh *m) {
+  if (!m) { set_error("null mesh"); return CHNS_ERR_ARG; }
+  return validate_mesh(m);
 }
 
 chns_status chns_energy_mass(const chns_mesh *mc, const chns_params *p, const double *U, double *energy,

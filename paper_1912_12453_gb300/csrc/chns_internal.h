@@ -43,19 +43,29 @@ struct PhysCoef {
   double g[3];
   double ext[3];                   // box extent per axis
   double lo[3];
+  // fields solved for (bit k: field k of [v_1..v_d, p, phi, mu]); the rows of
+  // the other fields are identity rows of J.w (block iteration, Sec. 3.1)
+  uint32_t fmask;
 };
 
 PhysCoef make_coef(const chns_params &p, const double *lo, const double *hi);
+
+struct Multigrid;
+void mg_release(Multigrid *g);
+// parameter checks shared by the entry points (dimension match, positivity)
+chns_status check_params(const chns_mesh *m, const chns_params *p);
 
 // Solver scratch, sized on first use.
 struct Workspace {
   DevBuf ut, dl, ut32, dl32, f;        // prepared nodal fields (time averages / increments)
   DevBuf F, dU, r;                     // double n_dof
+  DevBuf Ublk;                         // double n_dof: the previous block-iteration state
   DevBuf V;                            // double (m+1) n_dof Krylov basis
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors
   DevBuf e32, e64;                     // element-local J.w contributions (n_elem * 2^dim * nf)
   DevBuf ctr;                          // grid-reduction tickets
+  DevBuf count;                        // diagnostic counter (tau_m floors)
   DevBuf binv;                         // n_nodes * nf * nf inverse diagonal blocks (element precision)
   DevBuf binv64;                       // the same blocks in double (FP64 J.w iterations)
   DevBuf red;                          // reduction partials
@@ -64,7 +74,8 @@ struct Workspace {
   // preconditioner kept across steps: valid for `pc_steps_left` more steps
   // with the same precision, parameters and coarse level
   int pc_steps_left = 0;
-  int pc_precision = -1, pc_coarse = -1;
+  int pc_precision = -1, pc_coarse = -1, pc_kind = -1, pc_smooth = -1;
+  double pc_omega = -1.0;
   chns_params pc_params{};
   // CUDA graphs of the Arnoldi steps, one per step index and element
   // precision (0 float, 1 double), valid while `key` (the pointers and
@@ -151,8 +162,14 @@ struct chns_mesh {
   int32_t *gent = nullptr;
   uint8_t *nflag = nullptr;            // n_nodes
   int device = 0;
+  // FP32 J.w schedule picked by the autotuner (0 until tuned), its measured
+  // times per schedule (ms; negative: not measured)
+  int jv_variant = 0;
+  bool jv_tuned = false;
+  double jv_times[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   chns::Workspace ws;
   chns::Coarse coarse;
+  chns::Multigrid *mg = nullptr;       // multigrid hierarchy (built on first use)
 };
 
 // Instances of one dimension fused into a union mesh.

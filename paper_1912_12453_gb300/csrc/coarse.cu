@@ -307,7 +307,8 @@ __global__ void k_coarse_matvec(const T *__restrict__ Minv, int64_t ld, int64_t 
 }
 
 // z = Binv v + P zc  (nodal block-Jacobi plus the prolonged coarse
-// correction; zc == nullptr: block-Jacobi only)
+// correction; zc == nullptr: block-Jacobi only; Binv == nullptr: the coarse
+// correction only)
 template <typename T, int NF, int DIM>
 __global__ void __launch_bounds__(kB) k_block_prolong(CGeo g, const float *__restrict__ pos,
                                                       const int32_t *__restrict__ node_inst,
@@ -337,6 +338,11 @@ __global__ void __launch_bounds__(kB) k_block_prolong(CGeo g, const float *__res
 #pragma unroll
         for (int q = 0; q < NF; ++q) acc[q] = fma(wc, zp[q], acc[q]);
       }
+    }
+    if (!Binv) {  // coarse correction only
+#pragma unroll
+      for (int r = 0; r < NF; ++r) z[i * NF + r] = acc[r];
+      continue;
     }
     T B[NF * NF];
     if constexpr ((NF * NF * sizeof(T)) % 16 == 0) {
@@ -510,8 +516,11 @@ chns_status coarse_setup(chns_mesh *m, int Lc) {
   Coarse &C = m->coarse;
   if (C.level == Lc && C.pos) return CHNS_OK;
   C.release();
-  if (Lc < 1 || Lc > m->min_level - 1) {
-    set_error("coarse level %d must be in [1, %d] (one below the coarsest leaf level)", Lc, m->min_level - 1);
+  // a uniform mesh may be its own coarse grid (P = I, A_c = J: an exact solve)
+  const int lc_max = m->uniform ? m->min_level : m->min_level - 1;
+  if (Lc < 1 || Lc > lc_max) {
+    set_error("coarse level %d must be in [1, %d] (below the coarsest leaf level, or equal on a uniform mesh)",
+              Lc, lc_max);
     return CHNS_ERR_ARG;
   }
   const int dim = m->dim, nf = m->nf, ni = m->n_inst;

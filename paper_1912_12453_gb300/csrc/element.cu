@@ -272,10 +272,11 @@ template <int D> __device__ __forceinline__ int hidx(int i, int j) {
 }
 
 // Weak-form coefficients at one Gauss point: the row of test function N_a
-// receives W (N_a Sq[k] + sum_j d_j N_a Vq[k][j]) for equation k.
+// receives W (N_a Sq[k] + sum_j d_j N_a Vq[k][j]) for equation k.  floored:
+// whether the tau_m radicand was raised to 4/dt^2.
 template <int D, typename T, typename S>
 __device__ __forceinline__ void gp_physics(const KCoef<T> &c, const T *G, T CI_GG, T inv_trG,
-                                           const GpIn<D, S> &q, S *Sq, S (*Vq)[D]) {
+                                           const GpIn<D, S> &q, S *Sq, S (*Vq)[D], bool &floored) {
   // phi* clip (Eq. phi_for_density) and mixture properties at t_{k+1}
   const T pn = val(q.phin);
   const bool inside = fabs(pn) <= T(1);
@@ -299,7 +300,8 @@ __device__ __forceinline__ void gp_physics(const KCoef<T> &c, const T *G, T CI_G
   }
   S visc = eta * inv_rho * c.inv_Re;
   S rad = vGv + vGJ * inv_rho * c.inv_Pe + CI_GG * (visc * visc) + c.four_dt2;
-  if (val(rad) < c.four_dt2) rad = S(c.four_dt2);
+  floored = val(rad) < c.four_dt2;
+  if (floored) rad = S(c.four_dt2);
   S tau = rsqrt_(rad);
   S tau_c = inv_trG * rcp_(tau);
   // strong residuals
@@ -386,9 +388,13 @@ KCoef<T> kcoef(const PhysCoef &p) {
 }
 
 // ---------------------------------------------------------------- the element kernel
-// MODE 0: residual (output O = double), MODE 1: J.w (output O = T).
-template <int D, typename T, int MODE, bool HASF, typename O>
-__global__ void __launch_bounds__(128, 6) k_element(
+// MODE 0: residual (output O = double), MODE 1: J.w into the element-local
+// slots (O = T), MODE 2: count of the Gauss points whose tau_m radicand is
+// floored (O = unsigned long long, one counter), MODE 3: J.w scattered into
+// the node vector (O = T; one launch per element colour).  BS, MINB: block
+// size and minimum resident blocks per SM (the register budget).
+template <int D, typename T, int MODE, bool HASF, typename O, int BS = 128, int MINB = 6>
+__global__ void __launch_bounds__(BS, MINB) k_element(
     const int32_t *__restrict__ conn, const uint8_t *__restrict__ level,
     const int32_t *__restrict__ hang, int64_t e_begin, int64_t e_end,
     const T *__restrict__ ut, const T *__restrict__ dl, const T *__restrict__ w,
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(128, 6) k_element(
   gather<NF>(cn, hang, ut, u);
   gather<ND>(cn, hang, dl, d);
   T wn[NF];
-  if (MODE == 1) gather<NF>(cn, hang, w, wn);
+  if (MODE == 1 || MODE == 3) gather<NF>(cn, hang, w, wn);
   T fn[NF];
   if (HASF) gather<NF>(cn, hang, f, fn);
 
@@ -442,7 +448,8 @@ __global__ void __launch_bounds__(128, 6) k_element(
   for (int k = 0; k < NF; ++k) fq[k] = HASF ? ip_v<D>(fn[k], s) : T(0);
 
   T r[NF];
-  if (MODE == 0) {
+  bool floored = false;
+  if (MODE == 0 || MODE == 2) {
     GpIn<D, T> q;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -465,7 +472,12 @@ __global__ void __launch_bounds__(128, 6) k_element(
 #pragma unroll
     for (int k = 0; k < NF; ++k) q.f[k] = fq[k];
     T Sq[NF], Vq[NF][D];
-    gp_physics<D, T, T>(c, G, CI_GG, inv_trG, q, Sq, Vq);
+    gp_physics<D, T, T>(c, G, CI_GG, inv_trG, q, Sq, Vq, floored);
+    if constexpr (MODE == 2) {
+      const unsigned b = __ballot_sync(FULL, floored && active);
+      if ((threadIdx.x & 31) == 0 && b) atomicAdd(reinterpret_cast<unsigned long long *>(out), (unsigned long long)__popc(b));
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       T Vk[D];
@@ -500,7 +512,7 @@ __global__ void __launch_bounds__(128, 6) k_element(
 #pragma unroll
     for (int k = 0; k < NF; ++k) q.f[k] = Dl<T>(fq[k]);
     Dl<T> Sq[NF], Vq[NF][D];
-    gp_physics<D, T, Dl<T>>(c, G, CI_GG, inv_trG, q, Sq, Vq);
+    gp_physics<D, T, Dl<T>>(c, G, CI_GG, inv_trG, q, Sq, Vq, floored);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       T Vk[D];
@@ -509,23 +521,23 @@ __global__ void __launch_bounds__(128, 6) k_element(
       r[k] = contract<D>(W * Sq[k].d, Vk, s);
     }
   }
-  if (MODE == 1) {
+  if constexpr (MODE == 1) {
     // J.w: element-local output, slot (e, corner); k_gather_nodes sums the
     // slots of each node in a fixed order
     if (active) store_block<NF>(reinterpret_cast<T *>(out) + (e * NC + lc) * NF, r);
-    return;
-  }
-  // Lanes of one element may reach the same node: a hanging corner's parents
-  // can be corners of the element or parents of its other hanging corner.
-  // Warps that hold a hanging corner scatter one corner index at a time.
-  if (__any_sync(FULL, cn < 0)) {
+  } else if constexpr (MODE == 0 || MODE == 3) {
+    // Lanes of one element may reach the same node: a hanging corner's parents
+    // can be corners of the element or parents of its other hanging corner.
+    // Warps that hold a hanging corner scatter one corner index at a time.
+    if (__any_sync(FULL, cn < 0)) {
 #pragma unroll 1
-    for (int k = 0; k < NC; ++k) {
-      if (active && lc == k) scatter<NF>(cn, hang, out, r);
-      __syncwarp();
+      for (int k = 0; k < NC; ++k) {
+        if (active && lc == k) scatter<NF>(cn, hang, out, r);
+        __syncwarp();
+      }
+    } else if (active) {
+      scatter<NF>(cn, hang, out, r);
     }
-  } else if (active) {
-    scatter<NF>(cn, hang, out, r);
   }
 }
 
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(256) k_gather_nodes(const int32_t *__restrict_
                                                       const int32_t *__restrict__ gent,
                                                       const uint8_t *__restrict__ nflag, int64_t n_nodes,
                                                       const T *__restrict__ E, const T *__restrict__ w,
-                                                      T *__restrict__ y) {
+                                                      T *__restrict__ y, uint32_t fmask) {
   constexpr int NF = D + 3, G = 8;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_nodes; i += int64_t(gridDim.x) * blockDim.x) {
     T acc[NF];
@@ -585,7 +597,27 @@ __global__ void __launch_bounds__(256) k_gather_nodes(const int32_t *__restrict_
 #pragma unroll
       for (int k = 0; k < D; ++k) acc[k] = w[i * NF + k];
     if (fl & 2) acc[D] = w[i * NF + D];
+    if (fmask != 0xffu)
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (!((fmask >> k) & 1u)) acc[k] = w[i * NF + k];
     store_block<NF>(y + i * NF, acc);
+  }
+}
+
+// J.w by colour scatter: the constrained rows and the rows of fields outside
+// fmask become y = w (as k_gather_nodes does after its sums)
+template <int D, typename T>
+__global__ void k_fix_rows(const uint8_t *__restrict__ nflag, int64_t n_nodes, const T *__restrict__ w,
+                           T *__restrict__ y, uint32_t fmask) {
+  constexpr int NF = D + 3;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_nodes; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint8_t fl = nflag[i];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const bool keep = ((fmask >> k) & 1u) && !((fl & 1) && k < D) && !((fl & 2) && k == D);
+      if (!keep) y[i * NF + k] = w[i * NF + k];
+    }
   }
 }
 
@@ -702,6 +734,7 @@ PhysCoef make_coef(const chns_params &p, const double *lo, const double *hi) {
     c.ext[a] = hi[a] - lo[a];
     c.lo[a] = lo[a];
   }
+  c.fmask = 0xffu;
   return c;
 }
 
@@ -711,6 +744,8 @@ inline unsigned grid_for(int64_t threads) { return (unsigned)((threads + kBlock 
 // element kernels: 128 threads (16 leaves in 3D), 6 blocks per SM (measured
 // slightly ahead of 256 x 3 on the uniform and the adaptive meshes)
 constexpr int kElemBlock = 128;
+// FP64 element kernels: 3 blocks of 128 threads per SM (up to 170 registers)
+constexpr int kFp64MinBlocks = 3;
 inline unsigned grid_elem(int64_t threads) { return (unsigned)((threads + kElemBlock - 1) / kElemBlock); }
 inline unsigned grid_nodes(int64_t n) {
   int64_t b = (n + kBlock - 1) / kBlock;
@@ -731,10 +766,11 @@ template <int D, typename T, int MODE, bool HASF, typename O>
 void element_pass(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w,
                   const T *f, O *out, cudaStream_t st, int colour_lo, int colour_hi) {
   KCoef<T> c = kcoef<T>(pc);
+  constexpr int MINB = sizeof(T) == 8 ? kFp64MinBlocks : 6;
   for (int col = colour_lo; col < colour_hi; ++col) {
     int64_t b = m->colour_start[col], e = m->colour_start[col + 1];
     if (e <= b) continue;
-    k_element<D, T, MODE, HASF, O><<<grid_elem((e - b) << D), kElemBlock, 0, st>>>(
+    k_element<D, T, MODE, HASF, O, 128, MINB><<<grid_elem((e - b) << D), kElemBlock, 0, st>>>(
         m->conn, m->level, m->hang, b, e, ut, dl, w, f, out, c,
         reinterpret_cast<const KCoef<T> *>(sizeof(T) == 8 ? m->coef64 : m->coef32), m->elem_inst);
     note_launches(1);
@@ -753,30 +789,96 @@ void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, c
   }
 }
 
-// J.w in two launches: all elements at once into the element-local buffer E
-// (n_elem * 2^dim * nf values of T), then the node gather with the
-// constrained rows (no colouring, no output zeroing)
-template <typename T>
-void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *E, T *y,
-                   cudaStream_t st) {
-  KCoef<T> c = kcoef<T>(pc);
-  const KCoef<T> *tab = reinterpret_cast<const KCoef<T> *>(sizeof(T) == 8 ? m->coef64 : m->coef32);
-  const unsigned gn = grid_nodes(m->n_nodes);
-  if (m->dim == 2) {
-    k_element<2, T, 1, false, T><<<grid_elem(m->n_elem << 2), kElemBlock, 0, st>>>(
-        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, w, nullptr, E, c, tab, m->elem_inst);
-    k_gather_nodes<2, T><<<gn, kBlock, 0, st>>>(m->gptr, m->gent, m->nflag, m->n_nodes, E, w, y);
-  } else {
-    k_element<3, T, 1, false, T><<<grid_elem(m->n_elem << 3), kElemBlock, 0, st>>>(
-        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, w, nullptr, E, c, tab, m->elem_inst);
-    k_gather_nodes<3, T><<<gn, kBlock, 0, st>>>(m->gptr, m->gent, m->nflag, m->n_nodes, E, w, y);
-  }
+// J.w schedules (chosen per mesh by the autotuner, FP32 only; FP64 always
+// uses schedule 0):
+//   0: all elements at once into the element-local buffer E (n_elem * 2^dim
+//      * nf values of T), 128-thread blocks, 6 per SM; then the node gather
+//      with the constrained rows (no colouring, no output zeroing)
+//   1: as 0 with 256-thread blocks, 3 per SM
+//   2: as 0 with 64-thread blocks, 12 per SM
+//   3: as 0 with 128-thread blocks, 8 per SM (at most 64 registers)
+//   4: element colours one launch after another, each element adding its
+//      contributions into y (disjoint nodes within a colour; no E buffer),
+//      then the constrained rows
+//   5: as 0 with 128-thread blocks, 5 per SM (up to 102 registers)
+//   6: as 0 with 128-thread blocks, 4 per SM (up to 128 registers)
+template <int D, typename T, int BS, int MINB>
+static void jv_elemlocal(const chns_mesh *m, const KCoef<T> &c, const KCoef<T> *tab, const T *ut, const T *dl,
+                         const T *w, T *E, T *y, uint32_t fmask, cudaStream_t st) {
+  const int64_t threads = m->n_elem << D;
+  k_element<D, T, 1, false, T, BS, MINB><<<(unsigned)((threads + BS - 1) / BS), BS, 0, st>>>(
+      m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, w, nullptr, E, c, tab, m->elem_inst);
+  k_gather_nodes<D, T><<<grid_nodes(m->n_nodes), kBlock, 0, st>>>(m->gptr, m->gent, m->nflag, m->n_nodes, E, w, y,
+                                                                  fmask);
   note_launches(2);
 }
+
+template <int D, typename T>
+static void jv_colours(const chns_mesh *m, const KCoef<T> &c, const KCoef<T> *tab, const T *ut, const T *dl,
+                       const T *w, T *y, uint32_t fmask, cudaStream_t st) {
+  cudaMemsetAsync(y, 0, sizeof(T) * m->n_nodes * (D + 3), st);
+  for (int col = 0; col < m->n_colours; ++col) {
+    const int64_t b = m->colour_start[col], e = m->colour_start[col + 1];
+    if (e <= b) continue;
+    k_element<D, T, 3, false, T><<<grid_elem((e - b) << D), kElemBlock, 0, st>>>(
+        m->conn, m->level, m->hang, b, e, ut, dl, w, nullptr, y, c, tab, m->elem_inst);
+    note_launches(1);
+  }
+  k_fix_rows<D, T><<<grid_nodes(m->n_nodes), kBlock, 0, st>>>(m->nflag, m->n_nodes, w, y, fmask);
+  note_launches(1);
+}
+
+template <int D, typename T>
+static void jv_dispatch(const chns_mesh *m, int variant, const KCoef<T> &c, const KCoef<T> *tab, const T *ut,
+                        const T *dl, const T *w, T *E, T *y, uint32_t fmask, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    switch (variant) {
+      case 1: jv_elemlocal<D, T, 256, 3>(m, c, tab, ut, dl, w, E, y, fmask, st); return;
+      case 2: jv_elemlocal<D, T, 64, 12>(m, c, tab, ut, dl, w, E, y, fmask, st); return;
+      case 3: jv_elemlocal<D, T, 128, 8>(m, c, tab, ut, dl, w, E, y, fmask, st); return;
+      case 4: jv_colours<D, T>(m, c, tab, ut, dl, w, y, fmask, st); return;
+      case 5: jv_elemlocal<D, T, 128, 5>(m, c, tab, ut, dl, w, E, y, fmask, st); return;
+      case 6: jv_elemlocal<D, T, 128, 4>(m, c, tab, ut, dl, w, E, y, fmask, st); return;
+      default: break;
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    // FP64: bound by the narrow FP64 pipe, so occupancy matters less than
+    // the register spills a 6-blocks-per-SM budget causes
+    jv_elemlocal<D, T, 128, kFp64MinBlocks>(m, c, tab, ut, dl, w, E, y, fmask, st);
+  } else {
+    jv_elemlocal<D, T, 128, 6>(m, c, tab, ut, dl, w, E, y, fmask, st);
+  }
+}
+
+template <typename T>
+void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *E, T *y,
+                   cudaStream_t st, int variant) {
+  KCoef<T> c = kcoef<T>(pc);
+  const KCoef<T> *tab = reinterpret_cast<const KCoef<T> *>(sizeof(T) == 8 ? m->coef64 : m->coef32);
+  if (variant < 0) variant = sizeof(T) == 4 ? m->jv_variant : 0;
+  if (m->dim == 2) jv_dispatch<2, T>(m, variant, c, tab, ut, dl, w, E, y, pc.fmask, st);
+  else jv_dispatch<3, T>(m, variant, c, tab, ut, dl, w, E, y, pc.fmask, st);
+}
 template void launch_jacvec<float>(const chns_mesh *, const PhysCoef &, const float *, const float *,
-                                   const float *, float *, float *, cudaStream_t);
+                                   const float *, float *, float *, cudaStream_t, int);
 template void launch_jacvec<double>(const chns_mesh *, const PhysCoef &, const double *, const double *,
-                                    const double *, double *, double *, cudaStream_t);
+                                    const double *, double *, double *, cudaStream_t, int);
+
+// Gauss points with a floored tau_m radicand, added to *count (all elements
+// in one launch, FP64 physics as in the residual)
+void launch_tau_floor_count(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
+                            unsigned long long *count, cudaStream_t st) {
+  KCoef<double> c = kcoef<double>(pc);
+  const KCoef<double> *tab = reinterpret_cast<const KCoef<double> *>(m->coef64);
+  if (m->dim == 2)
+    k_element<2, double, 2, false, unsigned long long><<<grid_elem(m->n_elem << 2), kElemBlock, 0, st>>>(
+        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, nullptr, nullptr, count, c, tab, m->elem_inst);
+  else
+    k_element<3, double, 2, false, unsigned long long><<<grid_elem(m->n_elem << 3), kElemBlock, 0, st>>>(
+        m->conn, m->level, m->hang, 0, m->n_elem, ut, dl, nullptr, nullptr, count, c, tab, m->elem_inst);
+  note_launches(1);
+}
 
 void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st) {
   int64_t n = std::max<int64_t>(std::max(m->n_wall, m->n_pins), 1);

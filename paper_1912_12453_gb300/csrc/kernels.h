@@ -14,9 +14,14 @@ template <typename T>
 void launch_prep(const chns_mesh *m, const double *Un, const double *Uo, T *ut, T *dl, cudaStream_t st);
 void launch_residual(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
                      const double *f, double *F, cudaStream_t st);
+// J.w with schedule `variant` (-1: the mesh's tuned schedule for float,
+// schedule 0 for double); see element.cu for the schedules
+constexpr int kJacvecVariants = 7;
 template <typename T>
 void launch_jacvec(const chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *w, T *E, T *y,
-                   cudaStream_t st);
+                   cudaStream_t st, int variant = -1);
+void launch_tau_floor_count(const chns_mesh *m, const PhysCoef &pc, const double *ut, const double *dl,
+                            unsigned long long *count, cudaStream_t st);
 void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc, double *F, cudaStream_t st);
 int64_t energy_blocks(const chns_mesh *m);
 // per-instance element coefficients of a batched (union) mesh

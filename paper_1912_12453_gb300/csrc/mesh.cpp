@@ -9,6 +9,7 @@
 #include <numeric>
 
 #include "chns_internal.h"
+#include "host_util.h"
 
 namespace chns {
 
@@ -76,87 +77,6 @@ Workspace::~Workspace() {
   for (auto e : tev) cudaEventDestroy(e);
   if (hpinned) cudaFreeHost(hpinned);
 }
-
-namespace {
-
-// Open-addressing hash map from a 64-bit key to a 32-bit value.
-class KeyMap {
- public:
-  explicit KeyMap(size_t expected) {
-    size_t cap = 16;
-    while (cap < expected * 2) cap <<= 1;
-    keys_.assign(cap, kEmpty);
-    vals_.assign(cap, 0);
-    mask_ = cap - 1;
-  }
-  // returns (value, inserted)
-  std::pair<int64_t, bool> insert(uint64_t key, int64_t value) {
-    size_t i = hash(key) & mask_;
-    while (true) {
-      if (keys_[i] == kEmpty) {
-        keys_[i] = key;
-        vals_[i] = value;
-        ++size_;
-        return {value, true};
-      }
-      if (keys_[i] == key) return {vals_[i], false};
-      i = (i + 1) & mask_;
-    }
-  }
-  int64_t find(uint64_t key) const {
-    size_t i = hash(key) & mask_;
-    while (true) {
-      if (keys_[i] == kEmpty) return -1;
-      if (keys_[i] == key) return vals_[i];
-      i = (i + 1) & mask_;
-    }
-  }
-  size_t size() const { return size_; }
-
- private:
-  static constexpr uint64_t kEmpty = ~uint64_t(0);
-  static uint64_t hash(uint64_t x) {
-    x += 0x9e3779b97f4a7c15ull;
-    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-    return x ^ (x >> 31);
-  }
-  std::vector<uint64_t> keys_;
-  std::vector<int64_t> vals_;
-  size_t mask_ = 0, size_ = 0;
-};
-
-inline uint64_t pack(const int64_t *x, int dim) {
-  uint64_t k = 0;
-  for (int a = 0; a < dim; ++a) k |= uint64_t(x[a]) << (21 * a);
-  return k;
-}
-
-// octant key: the doubled coordinates of its centre, 2 x + s (unique per
-// octant, < 2^21 per axis for max_level <= 20)
-inline uint64_t okey(int level, const int64_t *x, int dim, int max_level) {
-  int64_t c[3];
-  int64_t s = int64_t(1) << (max_level - level);
-  for (int a = 0; a < dim; ++a) c[a] = 2 * x[a] + s;
-  return pack(c, dim);
-}
-
-uint64_t morton(const uint32_t *a, int dim, int max_level) {
-  uint64_t k = 0;
-  for (int b = 0; b <= max_level; ++b)
-    for (int ax = 0; ax < dim; ++ax) k |= uint64_t((a[ax] >> b) & 1u) << (dim * b + ax);
-  return k;
-}
-
-template <class T>
-chns_status upload(T **dst, const std::vector<T> &src) {
-  if (src.empty()) { *dst = nullptr; return CHNS_OK; }
-  CHNS_CUDA_TRY(cudaMalloc((void **)dst, sizeof(T) * src.size()));
-  CHNS_CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
-  return CHNS_OK;
-}
-
-}  // namespace
 
 chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor,
                        int max_level, const double lo[3], const double hi[3], chns_mesh *m) {
@@ -495,12 +415,6 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
   return CHNS_OK;
 }
 
-template <class T>
-std::vector<T> download(const T *d, size_t n) {
-  std::vector<T> h(n);
-  if (n) cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost);
-  return h;
-}
 
 // Node gather lists of a built mesh (single or union): for every node, the
 // (element, corner) slots whose element-local J.w contribution it receives,
@@ -541,6 +455,85 @@ chns_status build_gather(chns_mesh *m) {
   if ((st = upload(&m->gptr, gptr)) != CHNS_OK) return st;
   if ((st = upload(&m->gent, gent)) != CHNS_OK) return st;
   if ((st = upload(&m->nflag, nflag)) != CHNS_OK) return st;
+  return CHNS_OK;
+}
+
+// Host-side validation of a built mesh (single or union) against its device
+// arrays: hanging constraints, colouring, node gather lists.
+chns_status validate_mesh(const chns_mesh *m) {
+  const int nc = 1 << m->dim;
+  const int64_t ns = m->n_elem * nc;
+  const std::vector<int32_t> conn = download(m->conn, size_t(ns));
+  const std::vector<int32_t> hang = download(m->hang, size_t(m->n_hang) * 4);
+  const std::vector<int32_t> gptr = download(m->gptr, size_t(m->n_nodes) + 1);
+  const std::vector<int32_t> gent = download(m->gent, size_t(gptr.empty() ? 0 : gptr.back()));
+  if (cudaGetLastError() != cudaSuccess) { set_error("validate: reading the mesh back failed"); return CHNS_ERR_CUDA; }
+  // hanging constraints: 2 (edge) or 4 (face) distinct independent parents
+  for (int64_t h = 0; h < m->n_hang; ++h) {
+    const int32_t *p = &hang[size_t(h) * 4];
+    const int np = p[2] < 0 ? 2 : 4;
+    if (p[2] < 0 && p[3] >= 0) { set_error("hanging node %lld: malformed parent list", (long long)h); return CHNS_ERR_MESH; }
+    for (int k = 0; k < np; ++k) {
+      if (p[k] < 0 || p[k] >= m->n_nodes) { set_error("hanging node %lld: parent out of range", (long long)h); return CHNS_ERR_MESH; }
+      for (int l = 0; l < k; ++l)
+        if (p[l] == p[k]) { set_error("hanging node %lld: repeated parent", (long long)h); return CHNS_ERR_MESH; }
+    }
+  }
+  for (int64_t s = 0; s < ns; ++s)
+    if (conn[s] >= m->n_nodes || (conn[s] < 0 && -conn[s] - 1 >= m->n_hang)) {
+      set_error("slot %lld: node index out of range", (long long)s);
+      return CHNS_ERR_MESH;
+    }
+  // colouring: elements of one colour have disjoint expanded footprints
+  if (m->colour_start.size() != size_t(m->n_colours) + 1 || m->colour_start.back() != m->n_elem) {
+    set_error("colour ranges do not cover the elements");
+    return CHNS_ERR_MESH;
+  }
+  std::vector<int64_t> owner(size_t(m->n_nodes), -1);
+  std::vector<int> owner_col(size_t(m->n_nodes), -1);
+  for (int c = 0; c < m->n_colours; ++c)
+    for (int64_t e = m->colour_start[c]; e < m->colour_start[c + 1]; ++e)
+      for (int k = 0; k < nc; ++k) {
+        const int32_t v = conn[e * nc + k];
+        int32_t fp[4] = {v, -1, -1, -1};
+        if (v < 0) std::memcpy(fp, &hang[size_t(-v - 1) * 4], sizeof(fp));
+        for (int q = 0; q < 4 && fp[q] >= 0; ++q) {
+          const int32_t i = fp[q];
+          if (owner_col[i] == c && owner[i] != e) {
+            set_error("colour %d: elements %lld and %lld both reach node %d", c, (long long)owner[i],
+                      (long long)e, i);
+            return CHNS_ERR_MESH;
+          }
+          owner_col[i] = c;
+          owner[i] = e;
+        }
+      }
+  // gather lists: exactly the slots reaching each node, increasing, weighted
+  std::vector<std::vector<uint32_t>> want(size_t(m->n_nodes));
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t v = conn[s];
+    if (v >= 0) {
+      want[v].push_back(uint32_t(s));
+    } else {
+      const int32_t *p = &hang[size_t(-v - 1) * 4];
+      const uint32_t code = p[2] < 0 ? 1u : 2u;
+      for (int k = 0; k < (p[2] < 0 ? 2 : 4); ++k) want[p[k]].push_back(uint32_t(s) | (code << 30));
+    }
+  }
+  for (int64_t i = 0; i < m->n_nodes; ++i) {
+    const int64_t b = gptr[i], e = gptr[i + 1];
+    if (e - b != (int64_t)want[i].size()) {
+      set_error("node %lld: gather list has %lld slots, %zu reach it", (long long)i, (long long)(e - b), want[i].size());
+      return CHNS_ERR_MESH;
+    }
+    for (int64_t t = b; t < e; ++t) {
+      if (uint32_t(gent[t]) != want[i][t - b]) { set_error("node %lld: gather entry %lld differs", (long long)i, (long long)(t - b)); return CHNS_ERR_MESH; }
+      if (t > b && (uint32_t(gent[t]) & 0x3fffffffu) <= (uint32_t(gent[t - 1]) & 0x3fffffffu)) {
+        set_error("node %lld: gather list not in increasing slot order", (long long)i);
+        return CHNS_ERR_MESH;
+      }
+    }
+  }
   return CHNS_OK;
 }
 

@@ -1,11 +1,11 @@
-// Non-tensor FMA pipe peaks of the GPU (FP32 and FP64): every thread runs
-// independent chains of fused multiply-adds on registers; flop = 2 per FMA.
-// The FP32 number is the roofline denominator of the FP32 element kernels,
-// the FP64 number that of the FP64 ones.
-//
-//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o fma_peak fma_peak.cu && ./fma_peak
-#include <cstdio>
+// Non-tensor FMA pipe peaks of the GPU, measured in the run that reports a
+// roofline fraction against them: every thread runs independent chains of
+// fused multiply-adds on registers (flop = 2 per FMA), all SMs busy, best of
+// five CUDA-event timings.  Built into libchns_peak.so, a library of its own
+// that only the benchmark loads; the solver does not use it.
 #include <cuda_runtime.h>
+
+namespace {
 
 template <typename T, int CH>
 __global__ void __launch_bounds__(256) k_fma(T *out, int iters, T a, T b) {
@@ -22,9 +22,9 @@ __global__ void __launch_bounds__(256) k_fma(T *out, int iters, T a, T b) {
 }
 
 template <typename T, int CH>
-double run(int blocks, int iters) {
+int run(int blocks, int iters, double *tflops) {
   T *out = nullptr;
-  cudaMalloc(&out, sizeof(T));
+  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess) return 1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -39,24 +39,21 @@ double run(int blocks, int iters) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) best = ms;
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   cudaFree(out);
-  return 2.0 * CH * double(iters) * blocks * 256 / (best * 1e-3) / 1e12;
+  *tflops = 2.0 * CH * double(iters) * blocks * 256 / (best * 1e-3) / 1e12;
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
-int main() {
-  int dev = 0, sms = 0, clk = 0;
-  cudaGetDevice(&dev);
+}  // namespace
+
+// FP32 and FP64 FMA peaks (TFLOP/s) of the current device; returns 0 on success.
+extern "C" int chns_peak_fma(double *fp32_tflops, double *fp64_tflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
   const int blocks = sms * 8;
-  const double f32 = run<float, 16>(blocks, 20000);
-  const double f64 = run<double, 16>(blocks, 500);
-  printf("{\"sms\": %d, \"max_clock_mhz\": %.0f, \"fp32_fma_tflops\": %.2f, \"fp64_fma_tflops\": %.3f}\n", sms,
-         clk / 1e3, f32, f64);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    printf("CUDA error: %s\n", cudaGetErrorString(e));
-    return 1;
-  }
-  return 0;
+  if (run<float, 16>(blocks, 20000, fp32_tflops)) return 1;
+  return run<double, 16>(blocks, 500, fp64_tflops);
 }

@@ -269,6 +269,44 @@ __global__ void k_lincomb(double a, const double *__restrict__ x, double b, cons
     z[t] = a * x[t] + b * y[t];
 }
 
+// zero the fields of each node block whose bit in fmask is clear
+__global__ void k_mask_fields(double *__restrict__ y, int64_t n_nodes, int nf, uint32_t fmask) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n_nodes * nf; t += int64_t(gridDim.x) * kB)
+    if (!((fmask >> (t % nf)) & 1u)) y[t] = 0.0;
+}
+
+// max over i of |x_i - y_i| as a per-block maximum, then the maximum of the
+// block maxima (order-independent: exact)
+__global__ void k_maxabs_diff(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                              double *__restrict__ partial) {
+  double m = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n; t += int64_t(gridDim.x) * kB)
+    m = fmax(m, fabs(x[t] - y[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(FULL, m, o));
+  __shared__ double sh[kB / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < kB / 32; ++w) r = fmax(r, sh[w]);
+    partial[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_max_partials(const double *__restrict__ partial, int nb, double *__restrict__ res) {
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmax(m, partial[b]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(FULL, m, o));
+  __shared__ double sh[kB / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    *res = r;
+  }
+}
+
 // keep field k of each node block, scaled; zero the others
 __global__ void k_mask_field(double *__restrict__ y, int64_t n_nodes, int nf, int k, double s) {
   for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n_nodes * nf; t += int64_t(gridDim.x) * kB)
@@ -293,9 +331,10 @@ __global__ void k_probe_get(const int32_t *__restrict__ nodes, int64_t cnt, int 
   }
 }
 
-// in-place inverse of each nf x nf nodal block (Gauss-Jordan, partial pivoting, double)
+// in-place scale * inverse of each nf x nf nodal block (Gauss-Jordan, partial
+// pivoting, double)
 template <typename T, int NF>
-__global__ void k_invert_blocks(T *__restrict__ B, int64_t n_nodes, int *__restrict__ bad) {
+__global__ void k_invert_blocks(T *__restrict__ B, int64_t n_nodes, int *__restrict__ bad, double scale) {
   int64_t a = blockIdx.x * int64_t(kB) + threadIdx.x;
   if (a >= n_nodes) return;
   double M[NF][2 * NF];
@@ -322,7 +361,7 @@ __global__ void k_invert_blocks(T *__restrict__ B, int64_t n_nodes, int *__restr
     }
   }
   for (int r = 0; r < NF; ++r)
-    for (int c = 0; c < NF; ++c) B[(a * NF + r) * NF + c] = T(M[r][NF + c]);
+    for (int c = 0; c < NF; ++c) B[(a * NF + r) * NF + c] = T(scale * M[r][NF + c]);
 }
 
 }  // namespace
@@ -418,6 +457,17 @@ void vec_lincomb(double a, const double *x, double b, const double *y, double *z
   note_launches(1);
 }
 
+void vec_mask_fields(double *y, int64_t n_nodes, int nf, uint32_t fmask, cudaStream_t st) {
+  k_mask_fields<<<grid_n(n_nodes * nf), kB, 0, st>>>(y, n_nodes, nf, fmask);
+  note_launches(1);
+}
+
+void vec_maxabs_diff(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st) {
+  k_maxabs_diff<<<kRedBlocks, kB, 0, st>>>(x, y, n, partial);
+  k_max_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, res);
+  note_launches(2);
+}
+
 void vec_mask_field(double *y, int64_t n_nodes, int nf, int k, double s, cudaStream_t st) {
   k_mask_field<<<grid_n(n_nodes * nf), kB, 0, st>>>(y, n_nodes, nf, k, s);
   note_launches(1);
@@ -437,12 +487,12 @@ template void probe_get<float>(const int32_t *, int64_t, int, int, const float *
 template void probe_get<double>(const int32_t *, int64_t, int, int, const double *, double *, cudaStream_t);
 
 template <typename T>
-void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, cudaStream_t st) {
+void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, double scale, cudaStream_t st) {
   unsigned g = (unsigned)((n_nodes + kB - 1) / kB);
-  if (nf == 5) { k_invert_blocks<T, 5><<<g, kB, 0, st>>>(B, n_nodes, bad); note_launches(1); }
-  else { k_invert_blocks<T, 6><<<g, kB, 0, st>>>(B, n_nodes, bad); note_launches(1); }
+  if (nf == 5) { k_invert_blocks<T, 5><<<g, kB, 0, st>>>(B, n_nodes, bad, scale); note_launches(1); }
+  else { k_invert_blocks<T, 6><<<g, kB, 0, st>>>(B, n_nodes, bad, scale); note_launches(1); }
 }
-template void invert_blocks<float>(float *, int64_t, int, int *, cudaStream_t);
-template void invert_blocks<double>(double *, int64_t, int, int *, cudaStream_t);
+template void invert_blocks<float>(float *, int64_t, int, int *, double, cudaStream_t);
+template void invert_blocks<double>(double *, int64_t, int, int *, double, cudaStream_t);
 
 }  // namespace chns

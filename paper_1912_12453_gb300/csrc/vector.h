@@ -39,11 +39,16 @@ void vec_combine(const T *Z, int64_t ld, int nz, const double *c, double *x, int
 void vec_axpby(double a, const double *x, double b, double *y, int64_t n, cudaStream_t st);
 void vec_lincomb(double a, const double *x, double b, const double *y, double *z, int64_t n, cudaStream_t st);
 void vec_mask_field(double *y, int64_t n_nodes, int nf, int k, double s, cudaStream_t st);
+// zero the fields whose bit in fmask is clear
+void vec_mask_fields(double *y, int64_t n_nodes, int nf, uint32_t fmask, cudaStream_t st);
+// *res = max_i |x_i - y_i| (partial: red_blocks() doubles)
+void vec_maxabs_diff(const double *x, const double *y, int64_t n, double *partial, double *res, cudaStream_t st);
 template <typename T>
 void probe_set(const int32_t *nodes, int64_t cnt, int nf, int f, T *w, cudaStream_t st);
 template <typename T>
 void probe_get(const int32_t *nodes, int64_t cnt, int nf, int f, const T *y, T *B, cudaStream_t st);
+// B <- scale * B^{-1} for each nf x nf nodal block
 template <typename T>
-void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, cudaStream_t st);
+void invert_blocks(T *B, int64_t n_nodes, int nf, int *bad, double scale, cudaStream_t st);
 
 }  // namespace chns

@@ -1,4 +1,5 @@
-"""Batched CN steps (instances fused into union meshes) against one-instance steps."""
+"""Batched CN steps (instances fused into union meshes) against the oracle's
+steps of each instance and against one-instance GPU steps."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,7 @@ def test_batch_step_matches_single_steps():
         u = torch.from_numpy(W.initial_state(m.coords, w).reshape(-1)).cuda()
         chns.init_mu(m, w.params, u)
         U0.append(u)
-    opts = chns.SolverOpts.make(precision="fp32", newton_rtol=1e-11, newton_atol=1e-16, krylov_rtol=1e-6,
+    opts = chns.SolverOpts.make(precision="fp32", newton_rtol=1e-13, newton_atol=1e-16, krylov_rtol=1e-6,
                                 newton_max_it=30)
     single = []
     for m, w, u in zip(meshes, wls, U0):
@@ -47,7 +48,19 @@ def test_batch_step_matches_single_steps():
     batch = chns.Batch(meshes, [w.params for w in wls])
     outs = [torch.empty_like(u) for u in U0]
     stats = batch.step(U0, outs, opts)
+    from oracle import oracle as O
     for i, (m, w) in enumerate(zip(meshes, wls)):
+        # the oracle's Newton root of the instance's own step (sparse direct solves)
+        om = O.OracleMesh(w.leaves)
+        g_of_o = W.match_nodes(m.coords_int, om.coords_int)
+        u0 = U0[i].cpu().numpy().reshape(-1, m.nf)[g_of_o].reshape(-1)
+        ref, _ = om.step(w.params, u0, rtol=1e-14, atol=1e-16)
+        got = outs[i].cpu().numpy().reshape(-1, m.nf)[g_of_o]
+        F0o = np.linalg.norm(om.residual(w.params, u0, u0))
+        assert np.linalg.norm(om.residual(w.params, got.reshape(-1), u0)) <= 1.05e-13 * F0o, i
+        dr = got - ref.reshape(-1, m.nf)
+        for k in [f for f in range(m.nf) if f != m.dim]:
+            assert np.linalg.norm(dr[:, k]) <= 1e-9 * max(np.linalg.norm(ref.reshape(-1, m.nf)[:, k]), 1e-12) + 1e-13, (i, k)
         # a root of the instance's own residual, and the same state as the single step
         F0 = chns.residual(m, w.params, U0[i], U0[i]).norm().item()
         Fb = chns.residual(m, w.params, outs[i], U0[i]).norm().item()

@@ -102,6 +102,49 @@ def test_jacvec_fp32_bulk(pairs, name):
     assert rel(p.to_oracle(got), ref) <= TOL32
 
 
+@pytest.mark.parametrize("name", MESHES)
+def test_mesh_check(pairs, name):
+    """Host-side validator: colours with disjoint expanded footprints, exact
+    node gather lists, well-formed hanging constraints."""
+    pairs[name].gm.check()
+
+
+@pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "band3"])
+def test_tau_floor_regime(pairs, name):
+    """States where the tau_m radicand falls below 4/dt^2 at many Gauss points
+    (large dt, small Pe, large Re, |phi| up to 1.5 so the phi* clip is active
+    too): both sides floor the same Gauss points, and the residual and J.w
+    (FP64 and FP32-bulk) still match the oracle."""
+    import torch
+    p = pairs[name]
+    prm = _params(p.om.dim, dt=1.0, Pe=0.05, Re=1e4)
+    Un = random_state(p.om.n_nodes, p.nf, 11, -1.5, 1.5)
+    Uo = random_state(p.om.n_nodes, p.nf, 12, -1.5, 1.5)
+    w = random_state(p.om.n_nodes, p.nf, 13, -1, 1)
+    n_ref = p.om.tau_floor_count(prm, Un, Uo)
+    n_gpu = p.chns.tau_floor_count(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo))
+    assert n_ref > 0 and n_gpu == n_ref
+    assert n_ref < p.om.n_elem << p.om.dim  # and not all of them: both branches are exercised
+    ref = p.om.residual(prm, Un, Uo)
+    got = p.chns.residual(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo))
+    assert rel(p.to_oracle(got), ref) <= TOL64
+    refj = p.om.jacvec(prm, Un, Uo, w)
+    gotj = p.chns.jacvec(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w))
+    assert rel(p.to_oracle(gotj), refj) <= TOL64
+    gotj32 = p.chns.jacvec(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32), precision="fp32")
+    assert rel(p.to_oracle(gotj32), refj) <= TOL32
+
+
+@pytest.mark.parametrize("name", ["u2_l3", "band3"])
+def test_tau_floor_absent_in_the_workload_regime(pairs, name):
+    """The droplet parameters and smooth states floor no Gauss point."""
+    p = pairs[name]
+    wl = W.workload("droplet2d_l5" if p.om.dim == 2 else "droplet3d_l6")
+    Uo, Un = physical_state(p.om, wl)
+    assert p.om.tau_floor_count(wl.params, Un, Uo) == 0
+    assert p.chns.tau_floor_count(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo)) == 0
+
+
 @pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "band3"])
 def test_energy_mass(pairs, name):
     p = pairs[name]
@@ -175,11 +218,13 @@ def test_step_matches_oracle(pairs, name, precision):
     assert abs(stats["mass_new"] - stats["mass_old"]) < 1e-12
 
 
-@pytest.mark.parametrize("name", ["droplet2d_l5", "bubble3d_l5_9"])
+@pytest.mark.parametrize("name", ["droplet2d_l5", "droplet3d_l6", "bubble3d_l5_9"])
 def test_workload_applies_match_oracle(name):
-    """The full-size meshes of the workloads (the 2D droplet and the adaptive
-    3D bubble with hanging nodes, 1.4M leaves): residual and J.w at the
-    initial state plus a seeded perturbation, every entry compared."""
+    """The full-size meshes of the workloads (the 2D droplet, the uniform
+    level-6 3D droplet the benchmark times, and the adaptive 3D bubble with
+    hanging nodes, 1.4M leaves), in the launch configuration the benchmark
+    uses: residual and J.w at the initial state plus a seeded perturbation,
+    every entry compared."""
     import torch
     from oracle import oracle as O
     from paper_1912_12453_gb300 import chns

@@ -1,12 +1,21 @@
-"""Mutation sweep of the oracle pins (run by hand: python tests/oracle_mutation_sweep.py).
-
-Plants one plausible mistake at a time in a copy of the oracle (a flipped
-sign, a dropped term, a swapped index, a wrong weight) and runs the oracle
-pin tests on the copy; every planted mistake must make some pin fail.
-Nothing is changed in the repository itself.
+"""Mutation test of the oracle's pins: one plausible mistake at a time (a
+flipped sign, a dropped term, a swapped index, a wrong weight, a broken dual
+number rule, a missing clip or floor) is planted in a copy of the oracle, and
+the pin tests run on the copy; every planted mistake must make a pin fail.
+The repository itself is not changed.  The mutants run in parallel, each in
+its own temporary copy (oracle, tests, the input generators).
 """
-import os, shutil, subprocess, sys, tempfile
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 M = [
  ("pspg_sign", "s += T(dNa[i]) * tau_m / rho * Rm[i]; // +(d_i q", "s = s - T(dNa[i]) * tau_m / rho * Rm[i]; // +(d_i q"),
  ("cross_sign", "s = s - T(Na) * cross;", "s += T(Na) * cross;"),
@@ -27,7 +36,7 @@ M = [
  ("hang_weight", "double w = 1.0 / (double)it->second.size();", "double w = 0.5;"),
  ("dual_sqrt", "return Dual(s, a.d / (2.0 * s));", "return Dual(s, a.d / s);"),
  ("deta_noclip", "deta[k] = inside ? T(gamma) * phin.du[k] : T(0.0);", "deta[k] = T(gamma) * phin.du[k];"),
- ("no_floor", "if (val(rad) < 4.0 / (dt * dt)) rad = T(4.0 / (dt * dt));", ""),
+ ("no_floor", "      rad = T(4.0 / (dt * dt));\n      if (floors)", "      if (floors)"),
  ("mu_Cn", "s += T(P.Cn * P.Cn) * T(dNa[i]) * dphit[i];", "s += T(P.Cn) * T(dNa[i]) * dphit[i];"),
  ("ch_mob", "dmut[i] / T(P.Pe * P.Cn);", "dmut[i] / T(P.Pe);"),
  ("energy_kin", "E += detJ * (0.5 * rho * v2", "E += detJ * (rho * v2"),
@@ -39,21 +48,33 @@ M = [
  ("phis_no_clip", "bool inside = std::fabs(val(phin.u)) <= 1.0;", "bool inside = true;"),
  ("rho_old_phi", "T rho = T(alpha) * phis + T(beta);\n    T eta", "T rho = T(alpha) * phio.u + T(beta);\n    T eta"),
 ]
-which = sys.argv[1:] or [m[0] for m in M]
-res = {}
-for name, a, b in M:
-    if name not in which: continue
-    d = tempfile.mkdtemp(prefix='mut_')
-    for sub in ['oracle','tests','paper_1912_12453_gb300']:
-        shutil.copytree(os.path.join(ROOT,sub), os.path.join(d,sub), ignore=shutil.ignore_patterns('*.so','__pycache__'))
-    p = os.path.join(d,'oracle','chns_oracle.cpp'); s = open(p).read()
-    assert s.count(a) >= 1, name
-    open(p,'w').write(s.replace(a,b,1))
-    r = subprocess.run([sys.executable,'-m','pytest','tests/test_oracle_vms_pins.py','tests/test_oracle_pins.py','-x','-q','-m','not gpu','-p','no:cacheprovider'],cwd=d,capture_output=True,text=True)
-    last = [l for l in r.stdout.splitlines() if l.startswith('FAILED')]
-    res[name] = (r.returncode, last[:1])
-    print(name, 'CAUGHT' if r.returncode!=0 else 'MISSED', last[:1], flush=True)
-    shutil.rmtree(d)
-missed = [k for k, v in res.items() if v[0] == 0]
-print(f"{len(res) - len(missed)}/{len(res)} planted mistakes caught", "missed: " + ", ".join(missed) if missed else "")
-sys.exit(1 if missed else 0)
+
+
+def _run(mut):
+    name, a, b = mut
+    d = tempfile.mkdtemp(prefix="mut_")
+    try:
+        ign = shutil.ignore_patterns("*.so", "__pycache__", "_build", "*.o", "csrc")
+        for sub in ("oracle", "tests", "paper_1912_12453_gb300"):
+            shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub), ignore=ign)
+        p = os.path.join(d, "oracle", "chns_oracle.cpp")
+        s = open(p).read()
+        if s.count(a) < 1:
+            return name, None, "pattern not found"
+        open(p, "w").write(s.replace(a, b, 1))
+        r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_vms_pins.py", "tests/test_oracle_pins.py",
+                            "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"],
+                           cwd=d, capture_output=True, text=True, timeout=600)
+        failed = [l for l in r.stdout.splitlines() if l.startswith("FAILED")]
+        return name, r.returncode != 0, failed[:1]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_is_caught():
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        res = list(ex.map(_run, M))
+    bad = [(n, why) for n, caught, why in res if caught is not True]
+    assert not bad, bad
+    assert len(res) == len(M) >= 30

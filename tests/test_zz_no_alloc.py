@@ -60,3 +60,26 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     U2 = torch.zeros(mesh2.n_dof, dtype=torch.float64, device="cuda")
     s = L.chns_energy_mass_noalloc(mesh2.handle, ctypes.byref(prm), U2.data_ptr(), out3.data_ptr(), None)
     assert s == 1 and b"too large" in L.chns_last_error()
+
+
+def test_noalloc_checks_parameters_like_the_allocating_entry_point():
+    """Both entry points accept and reject the same parameters: Cn = 0 or
+    Fr = 0 is an argument error (status 1), not a NaN in out3."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1912_12453_gb300 import chns
+    L = chns.lib()
+    mesh = chns.Mesh(W.uniform_leaves(2, 3))
+    U = torch.zeros(mesh.n_dof, dtype=torch.float64, device="cuda")
+    out3 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for bad in (dict(Cn=0.0), dict(Fr=0.0)):
+        kw = dict(dt=1e-3, Cn=0.04, Re=10.0, We=3.0, Pe=25.0, Fr=1.0, rho_ratio=0.1, eta_ratio=0.2)
+        kw.update(bad)
+        prm = chns.Params.of(W.Params(2, **kw))
+        e, m, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        assert L.chns_energy_mass(mesh.handle, ctypes.byref(prm), U.data_ptr(), ctypes.byref(e), ctypes.byref(m),
+                                  ctypes.byref(b), None) == 1
+        assert L.chns_energy_mass_noalloc(mesh.handle, ctypes.byref(prm), U.data_ptr(), out3.data_ptr(),
+                                          None) == 1
+
