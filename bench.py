@@ -292,17 +292,22 @@ def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier):
     finals = {}
     for name, opts in (("fp32_mixed", opts32), ("fp64", opts64)):
         Ua, Ub = U0.clone(), torch.empty_like(U0)
-        chns.step(mesh, wl.params, Ua, Ub, opts)  # warm-up (builds graphs and the preconditioner)
-        Ua.copy_(U0)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stats = []
-        e0.record()
-        for _ in range(steps):
-            stats.append(chns.step(mesh, wl.params, Ua, Ub, opts))
-            Ua, Ub = Ub, Ua
-        e1.record()
-        barrier()
+        try:
+            chns.step(mesh, wl.params, Ua, Ub, opts)  # warm-up (builds graphs and the preconditioner)
+            Ua.copy_(U0)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stats = []
+            e0.record()
+            for _ in range(steps):
+                stats.append(chns.step(mesh, wl.params, Ua, Ub, opts))
+                Ua, Ub = Ub, Ua
+            e1.record()
+            barrier()
+        except chns.ChnsError as ex:
+            out[name] = {"error": str(ex)}
+            log(name, wl.name, "failed:", ex)
+            continue
         ms = e0.elapsed_time(e1) / steps
         finals[name] = Ua.clone()
         out[name] = {"s_per_step": ms / 1e3, "newton_its": [s["newton_its"] for s in stats],
@@ -312,9 +317,77 @@ def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier):
                      "precond_ms_per_step": float(np.mean([s["precond_ms"] for s in stats])),
                      "fp64_newton_its": [s["fp64_newton_its"] for s in stats]}
         log(name, wl.name, f"{ms:.1f} ms/step", out[name]["newton_its"], out[name]["krylov_its"])
-    out["speedup_fp32_mixed_over_fp64"] = out["fp64"]["s_per_step"] / out["fp32_mixed"]["s_per_step"]
-    out["rel_diff_fp32_vs_fp64_per_field"] = field_diffs(finals["fp32_mixed"], finals["fp64"], mesh.nf, mesh.dim)
+    if len(finals) == 2:
+        out["speedup_fp32_mixed_over_fp64"] = out["fp64"]["s_per_step"] / out["fp32_mixed"]["s_per_step"]
+        out["rel_diff_fp32_vs_fp64_per_field"] = field_diffs(finals["fp32_mixed"], finals["fp64"], mesh.nf, mesh.dim)
     out["steps"] = steps
+    return out
+
+
+def compare_batch_steps(chns, n, steps, opts32, opts64, dev, barrier):
+    """The batched workload: n independent droplet / bubble instances of
+    uneven size and parameters (2D quadtrees to levels 6-9, 3D octrees to
+    levels 5-7) fused into one union mesh per dimension and advanced
+    together; FP32-bulk vs FP64 batch steps from the same state."""
+    import torch
+    wls = W.batched_workloads(n)
+    meshes = [chns.Mesh(w.leaves) for w in wls]
+    U0 = []
+    for m, w in zip(meshes, wls):
+        u = torch.from_numpy(W.initial_state(m.coords, w).reshape(-1)).to(dev)
+        chns.init_mu(m, w.params, u)
+        U0.append(u)
+    batch = chns.Batch(meshes, [w.params for w in wls])
+    out = {"instances": n, "dims": {"2": sum(1 for w in wls if w.params.dim == 2),
+                                    "3": sum(1 for w in wls if w.params.dim == 3)},
+           "leaves": int(sum(m.n_elem for m in meshes)), "n_dof": int(sum(m.n_dof for m in meshes)),
+           "steps": steps}
+    for name, opts in (("fp32_mixed", opts32), ("fp64", opts64)):
+        Ua = [u.clone() for u in U0]
+        Ub = [torch.empty_like(u) for u in U0]
+        try:
+            batch.step(Ua, Ub, opts)  # warm-up: graphs, hierarchy, preconditioner
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stats = []
+            e0.record()
+            for _ in range(steps):
+                stats.append(batch.step(Ua, Ub, opts))
+                Ua, Ub = Ub, Ua
+            e1.record()
+            barrier()
+        except chns.ChnsError as ex:
+            out[name] = {"error": str(ex)}
+            log("batch", name, "failed:", ex)
+            continue
+        ms = e0.elapsed_time(e1) / steps
+        worst = max(st[i]["res_final"] / st[i]["res0"] for st in stats for i in range(n) if st[i]["res0"] > 0)
+        # J.w rate: per dimension group (the instances of a group share its counters)
+        jv = {}
+        for i, w in enumerate(wls):
+            d = w.params.dim
+            g = jv.setdefault(d, {"dof": 0, "ms": 0.0, "calls": 0})
+            g["dof"] += meshes[i].n_dof
+        for d, g in jv.items():
+            i0 = next(i for i, w in enumerate(wls) if w.params.dim == d)
+            g["ms"] = sum(st[i0]["jacvec_ms"] for st in stats)
+            g["calls"] = sum(st[i0]["jacvec_calls"] for st in stats)
+        out[name] = {"s_per_step": ms / 1e3,
+                     "newton_its_per_group": [[st[i]["newton_its"] for st in stats] for i in
+                                              sorted({next(j for j, w in enumerate(wls) if w.params.dim == d)
+                                                      for d in jv})],
+                     "krylov_its_per_group": [[st[i]["krylov_its_total"] for st in stats] for i in
+                                              sorted({next(j for j, w in enumerate(wls) if w.params.dim == d)
+                                                      for d in jv})],
+                     "worst_instance_res_rel": worst,
+                     "jacvec_GDoFs": sum(g["dof"] * g["calls"] for g in jv.values()) /
+                                     max(1e-9, sum(g["ms"] for g in jv.values()) / 1e3) / 1e9}
+        log("batch", name, f"{ms:.1f} ms/step", out[name]["newton_its_per_group"], out[name]["krylov_its_per_group"])
+    if "s_per_step" in out.get("fp64", {}) and "s_per_step" in out.get("fp32_mixed", {}):
+        out["speedup_fp32_mixed_over_fp64"] = out["fp64"]["s_per_step"] / out["fp32_mixed"]["s_per_step"]
+    batch.close()
+    for m in meshes:
+        m.close()
     return out
 
 
@@ -326,6 +399,8 @@ def profile_applies(args):
     build.build()
     wl = W.workload(args.workload)
     mesh = chns.Mesh(wl.leaves)
+    if args.profile_schedule >= 0:
+        mesh.jacvec_schedule(args.profile_schedule)
     U0 = torch.from_numpy(W.initial_state(mesh.coords, wl).reshape(-1)).cuda()
     U1 = U0 + 1e-2 * torch.from_numpy(W.perturbation(mesh.n_nodes, mesh.nf, 1)[0].reshape(-1)).cuda()
     dt = torch.float32 if args.profile_precision == "fp32" else torch.float64
@@ -356,15 +431,20 @@ def main():
                     help="CN steps one preconditioner build serves (1: rebuilt every step); with the "
                          "defaults one rebuild falls inside the 5 timed steps")
     ap.add_argument("--workload", default=WORKLOAD, help="headline workload (droplet3d_l6)")
-    ap.add_argument("--extra", default="bubble3d_l5_9",
+    ap.add_argument("--extra", default="bubble3d_l5_9,batched64",
                     help="comma-separated further workloads for the FP32-vs-FP64 step comparison "
-                         "(bubble3d_l5_9, merge3d_l6_10; empty: none)")
+                         "(bubble3d_l5_9, merge3d_l6_10, batchedN = N batched instances; empty: none)")
     ap.add_argument("--extra-steps", type=int, default=2)
+    ap.add_argument("--preconditioner", default="multigrid", choices=["multigrid", "two_level"])
+    ap.add_argument("--mg-omega", type=float, default=0.4)
+    ap.add_argument("--mg-smooth", type=int, default=1)
+    ap.add_argument("--autotune", type=int, default=1, help="1: autotune the FP32 J.w schedule per mesh")
     ap.add_argument("--krylov-max-it", type=int, default=400)
     ap.add_argument("--krylov-restart", type=int, default=64)
     ap.add_argument("--profile-applies", type=int, default=0)
     ap.add_argument("--profile-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--profile-residual", action="store_true")
+    ap.add_argument("--profile-schedule", type=int, default=-1, help="FP32 J.w schedule to profile (-1: default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -440,12 +520,13 @@ def main():
     log(f"apply sweep: fp32 J.w {jv32_mean} ms, fp64 J.w {jv64_mean} ms, fp64 residual {res64_mean} ms")
 
     # ---- CN steps, FP32-bulk mixed (timed region)
+    pc_kw = dict(preconditioner=args.preconditioner, mg_omega=args.mg_omega, mg_smooth=args.mg_smooth)
     opts32 = chns.SolverOpts.make(precision="fp32", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
                                   krylov_restart=args.krylov_restart, krylov_max_it=args.krylov_max_it,
-                                  reuse_preconditioner=args.precond_steps)
+                                  reuse_preconditioner=args.precond_steps, autotune=bool(args.autotune), **pc_kw)
     opts64 = chns.SolverOpts.make(precision="fp64", newton_rtol=args.newton_rtol, krylov_rtol=1e-3,
                                   krylov_restart=args.krylov_restart, krylov_max_it=args.krylov_max_it,
-                                  reuse_preconditioner=args.precond_steps)
+                                  reuse_preconditioner=args.precond_steps, **pc_kw)
     Ua = U0.clone()
     Ub = torch.empty_like(Ua)
     for _ in range(args.warmup):
@@ -482,22 +563,28 @@ def main():
     stats64 = []
     step64_ms = None
     diff = None
+    fp64_error = None
     if k64 > 0:
-        Ua.copy_(U0)
-        chns.step(mesh, prm, Ua, Ub, opts64)  # warm-up
-        Ua.copy_(U0)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k64):
-            stats64.append(chns.step(mesh, prm, Ua, Ub, opts64))
-            Ua, Ub = Ub, Ua
-        e1.record(stream)
-        barrier()
-        step64_ms = e0.elapsed_time(e1) / k64
-        log("fp64 steps", [{k: st[k] for k in ("newton_its", "krylov_its_total", "seconds")} for st in stats64])
-        if k64 == args.steps:
-            diff = field_diffs(U32, Ua, mesh.nf, mesh.dim)
+        try:
+            Ua.copy_(U0)
+            chns.step(mesh, prm, Ua, Ub, opts64)  # warm-up
+            Ua.copy_(U0)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k64):
+                stats64.append(chns.step(mesh, prm, Ua, Ub, opts64))
+                Ua, Ub = Ub, Ua
+            e1.record(stream)
+            barrier()
+            step64_ms = e0.elapsed_time(e1) / k64
+            log("fp64 steps", [{k: st[k] for k in ("newton_its", "krylov_its_total", "seconds")} for st in stats64])
+            if k64 == args.steps:
+                diff = field_diffs(U32, Ua, mesh.nf, mesh.dim)
+        except chns.ChnsError as ex:
+            fp64_error = str(ex)
+            stats64 = []
+            log("fp64 steps failed:", ex)
 
     # ---- end to end through host buffers: H2D of U_n, the step, D2H of U_{n+1}
     host_in = torch.from_numpy(U0h.copy()).pin_memory()
@@ -541,6 +628,18 @@ def main():
     # ---- further workloads: FP32-bulk vs FP64 steps at the same tolerance
     extra = {}
     for name in [x for x in args.extra.split(",") if x]:
+        if name.startswith("batched"):
+            try:
+                extra[name] = compare_batch_steps(chns, int(name[len("batched"):] or 64), args.extra_steps,
+                                                  opts32, opts64, dev, barrier)
+                extra[name]["workload"] = ("batched droplet / bubble instances (2D quadtrees levels 6-9, 3D "
+                                           "octrees levels 5-7, radii U[0.1, 0.25], density ratios log-U[1e-3, 1], "
+                                           "viscosity ratios log-U[1e-2, 1], Cn 0.02), one union mesh per dimension")
+            except Exception as ex:
+                extra[name] = {"error": f"{type(ex).__name__}: {ex}"}
+                log(name, "failed:", ex)
+            torch.cuda.empty_cache()
+            continue
         try:
             wx = W.workload(name)
             mx = chns.Mesh(wx.leaves)
@@ -587,16 +686,22 @@ def main():
                                     "Newton iteration (FP64 residual and update)",
                        "newton_rtol": args.newton_rtol,
                        "krylov": f"FGMRES({args.krylov_restart})",
-                       "preconditioner": f"nodal block-Jacobi + Galerkin coarse space (uniform level "
-                                         f"min(3, coarsest leaf - 1)), built once per {args.precond_steps} CN steps "
+                       "preconditioner": (f"geometric multigrid V-cycle over the octree levels (coarsest uniform "
+                                          f"level 2 solved by a dense inverse), {args.mg_smooth} damped block-Jacobi "
+                                          f"sweep(s) omega {args.mg_omega}"
+                                          if args.preconditioner == "multigrid" else
+                                          "nodal block-Jacobi + Galerkin coarse space (uniform level min(3, coarsest "
+                                          "leaf - 1))") +
+                                         f"; built once per {args.precond_steps} CN steps "
                                          f"({sum(1 for s_ in stats32 if s_['precond_ms'] > 0)} builds inside the timed steps)",
+                       "jacvec_schedule": chns.JACVEC_VARIANTS[stats32[-1]["jacvec_variant"]],
                        "l2": f"inputs larger than L2: the step's Krylov basis is {args.krylov_restart + 1} x "
                              f"{n_dof * 4 / 1e6:.1f} MB = {basis_mb:.0f} MB of floats; the apply sweep flushes L2 "
                              f"(256 MB write) before every apply",
                        "parallelism": f"replicas x{world}"},
             "cn_step": {
                 "fp32_mixed": steps_first,
-                "fp64": None if not stats64 else {
+                "fp64": {"error": fp64_error} if fp64_error else None if not stats64 else {
                     "s_per_step": step64_ms / 1e3,
                     "newton_its": [s["newton_its"] for s in stats64],
                     "krylov_its": [s["krylov_its_total"] for s in stats64],

@@ -99,7 +99,9 @@ typedef struct {
                               3 in 2D */
   int mg_smooth;           /* multigrid: damped block-Jacobi sweeps before and after each coarse
                               correction (1..8) */
-  double mg_omega;         /* multigrid: damping of the block-Jacobi sweeps (0 < omega <= 1) */
+  double mg_omega;         /* multigrid: damping of the block-Jacobi sweeps (0 < omega <= 1; 0.4
+                              measured best on the droplet and bubble workloads, 0.6 and above
+                              let the smoother amplify some modes) */
   int block_iteration;     /* 0: coupled Newton on all fields; 1: the block iteration of Sec. 3.1
                               (Fig. flowchart_block): Newton on the Navier-Stokes fields (v, p) with
                               phi, mu frozen, then on the Cahn-Hilliard fields (phi, mu) with v, p

@@ -278,10 +278,11 @@ Field<T> interp(int dim, const Basis& B, const T* nodal, int stride, int comp) {
 // un, uo: local nodal values (nc x nf) of U^{k+1}, U^k; f: local nodal forcing
 // at t_{k+1/2} or null.  r: local residual (nc x nf), overwritten.
 // floors (nullable): incremented once per Gauss point whose tau_m radicand is
-// raised to 4/dt^2 (the reading of an unbounded radicand, see the header).
+// raised to 4/dt^2 (the reading of an unbounded radicand, see the header);
+// margin (nullable): lowered to |radicand dt^2 / 4 - 1| where smaller.
 template <class T>
 void element_residual(const Mesh& m, const Params& P, int64_t e, const T* un, const T* uo,
-                      const double* f, T* r, int64_t* floors = nullptr) {
+                      const double* f, T* r, int64_t* floors = nullptr, double* margin = nullptr) {
   const int dim = m.dim, nc = m.nc, nf = m.nf;
   const int IP = dim, IPHI = dim + 1, IMU = dim + 2;
   double h[3];
@@ -362,6 +363,7 @@ void element_residual(const Mesh& m, const Params& P, int64_t e, const T* un, co
     for (int i = 0; i < dim; ++i) { vGv += vt[i] * T(G[i]) * vt[i]; vGJ += vt[i] * T(G[i]) * J[i]; }
     T visc = eta / (rho * T(P.Re));
     T rad = T(4.0 / (dt * dt)) + vGv + vGJ / (rho * T(P.Pe)) + T(P.C_I) * visc * visc * T(GG);
+    if (margin) *margin = std::min(*margin, std::fabs(val(rad) * dt * dt / 4.0 - 1.0));
     if (val(rad) < 4.0 / (dt * dt)) {
       rad = T(4.0 / (dt * dt));
       if (floors) ++*floors;
@@ -625,18 +627,22 @@ int64_t oracle_jacobian_coo(void* h, const double* prm, const double* Un, const 
 }
 
 // Number of Gauss points (over all leaves) whose tau_m radicand is raised to
-// 4/dt^2, evaluated as in oracle_residual (double precision).
-int64_t oracle_tau_floor_count(void* h, const double* prm, const double* Un, const double* Uo) {
+// 4/dt^2, evaluated as in oracle_residual (double precision); margin
+// (nullable): the smallest |radicand dt^2 / 4 - 1| over all Gauss points, how
+// far the closest one is from the floor decision.
+int64_t oracle_tau_floor_count(void* h, const double* prm, const double* Un, const double* Uo, double* margin) {
   Mesh& m = *(Mesh*)h;
   Params P = unpack(prm);
   const int L = m.nc * m.nf;
   std::vector<double> un(L), uo(L), r(L);
   int64_t floors = 0;
+  double mg = 1e300;
   for (int64_t e = 0; e < m.n_elem; ++e) {
     gather<double>(m, e, Un, nullptr, un.data());
     gather<double>(m, e, Uo, nullptr, uo.data());
-    element_residual<double>(m, P, e, un.data(), uo.data(), nullptr, r.data(), &floors);
+    element_residual<double>(m, P, e, un.data(), uo.data(), nullptr, r.data(), &floors, &mg);
   }
+  if (margin) *margin = mg;
   return floors;
 }
 

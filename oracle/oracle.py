@@ -56,7 +56,7 @@ def lib():
         L.oracle_jacobian_coo.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.oracle_energy_mass.argtypes = [vp, vp, vp, vp]
         L.oracle_tau_floor_count.restype = i64
-        L.oracle_tau_floor_count.argtypes = [vp, vp, vp, vp]
+        L.oracle_tau_floor_count.argtypes = [vp, vp, vp, vp, vp]
         L.oracle_jacvec_threads.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         _lib = L
     return _lib
@@ -155,7 +155,15 @@ class OracleMesh:
     def tau_floor_count(self, params, Un, Uo) -> int:
         """Gauss points whose tau_m radicand is raised to 4/dt^2."""
         prm = _params_array(params)
-        return int(lib().oracle_tau_floor_count(self._h, _p(prm), _p(_vec(Un)), _p(_vec(Uo))))
+        return int(lib().oracle_tau_floor_count(self._h, _p(prm), _p(_vec(Un)), _p(_vec(Uo)), None))
+
+    def tau_floor_margin(self, params, Un, Uo) -> float:
+        """Smallest |radicand dt^2/4 - 1| over all Gauss points: the distance
+        of the closest one from the floor decision."""
+        prm = _params_array(params)
+        m = ctypes.c_double()
+        lib().oracle_tau_floor_count(self._h, _p(prm), _p(_vec(Un)), _p(_vec(Uo)), ctypes.byref(m))
+        return float(m.value)
 
     def jacobian(self, params, Un, Uo):
         import scipy.sparse as sp

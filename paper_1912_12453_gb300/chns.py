@@ -71,7 +71,7 @@ class SolverOpts(ctypes.Structure):
     def make(cls, precision="fp64", newton_rtol=1e-10, newton_atol=1e-13, newton_max_it=20,
              krylov_rtol=1e-4, krylov_restart=64, krylov_max_it=600, reuse_preconditioner=1,
              coarse_level=-1, use_graph=True, preconditioner="two_level", mg_coarsest=-1, mg_smooth=1,
-             mg_omega=0.7, block_iteration=False, block_tol=1e-4, block_max_it=50, autotune=False):
+             mg_omega=0.4, block_iteration=False, block_tol=1e-4, block_max_it=50, autotune=False):
         prec = CHNS_FP64 if precision == "fp64" else CHNS_FP32_BULK
         pcn = {"two_level": CHNS_PC_TWO_LEVEL, "multigrid": CHNS_PC_MULTIGRID}[preconditioner]
         return cls(newton_rtol, newton_atol, newton_max_it, krylov_rtol, krylov_restart, krylov_max_it,

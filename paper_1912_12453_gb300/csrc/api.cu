@@ -305,10 +305,18 @@ bool inject_krylov_fault() {
 // stream before the host waits for column j (two result slots, a pinned
 // mirror each): the GPU never idles on the host.  When step j converges,
 // the queued step j + 1 is discarded.
+// The FP32 multigrid hierarchy used as the preconditioner of a double
+// FGMRES (the FP64 finish of the mixed path): the V-cycle runs in float on
+// the float linearisation (ut32, dl32), between conversions of v and z.
+struct Mg32 {
+  const float *ut = nullptr, *dl = nullptr;
+  float *vin = nullptr, *zout = nullptr;
+};
+
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
                    bool mg, const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
-                   cudaStream_t st) {
+                   cudaStream_t st, const Mg32 *mg32 = nullptr) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
@@ -353,7 +361,12 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     double *h1 = hd + 3 * K * sl, *h2 = h1 + K, *nr = h1 + 2 * K;
     T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
     T *zj = Z + (int64_t)j * ld;
-    if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
+    if (mg32) {
+      const int64_t nn = m->n_nodes * m->nf;
+      vec_convert<T, float>(vj, mg32->vin, nn, 1.0, s);
+      TRY(mg_apply<float>(m, pc, mg32->ut, mg32->dl, mg32->vin, mg32->zout, s));
+      vec_convert<float, T>(mg32->zout, zj, nn, 1.0, s);
+    } else if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
     else precond_apply<T>(m, Binv, coarse, vj, zj, s);
     int ev = 0;
     if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j], s, cudaEventRecordExternal));
@@ -383,7 +396,8 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
     key.p[14] = ctr; key.p[15] = mg ? m->mg : nullptr;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
-    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph; key.i[7] = m->jv_variant;
+    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph + 2 * (mg32 != nullptr);
+    key.i[7] = m->jv_variant;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
     if (G.key.size() != sizeof(key) || std::memcmp(G.key.data(), kb, sizeof(key)) != 0) {
@@ -645,7 +659,12 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   double f0_all = -1.0, fn_last = 0.0;
 
   // Newton on the fields of fmask from the current U, to newton_rtol of its
-  // own initial residual (Sec. 3.5)
+  // initial residual (Sec. 3.5).  In the block iteration the reference is
+  // the initial residual of the first sub-solve of the same block: later
+  // sub-solves start close to their root, and a tolerance relative to their
+  // own tiny initial residual would ask for more than double precision holds.
+  double f0_block[2] = {-1.0, -1.0};
+  std::vector<double> fi0_block[2];
   auto solve = [&](uint32_t mask) -> chns_status {
     fmask = mask;
     PhysCoef pcs = pc;
@@ -655,10 +674,19 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
     if (mask != 0xffu) have_pc = false;  // the operator differs per block: build for each sub-solve
     double fn = 0.0;
     TRY(residual(&fn));
-    const double f0 = fn;
+    double f0 = fn;
     if (f0_all < 0.0) f0_all = f0;
     TRY(instance_norms());
     fi0 = fi;
+    if (mask != 0xffu) {
+      const int kind = (mask & 1u) ? 0 : 1;  // NS block holds v_1
+      if (f0_block[kind] < 0.0) {
+        f0_block[kind] = f0;
+        fi0_block[kind] = fi0;
+      }
+      f0 = std::max(f0, f0_block[kind]);
+      for (int q = 0; q < ni; ++q) fi0[q] = std::max(fi0[q], fi0_block[kind][q]);
+    }
     auto converged = [&]() {
       if (ni == 1) return fn <= std::max(o.newton_rtol * f0, o.newton_atol);
       for (int q = 0; q < ni; ++q)
@@ -711,15 +739,25 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
       } else {
         double *ut_t = nullptr, *dl_t = nullptr;
         TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
+        Mg32 mg32;
         if (mixed) {
-          if (use_mg) {  // the FP64 finish rebuilds the hierarchy's operators in double once
-            if (!have_pc64) {
-              TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
-              have_pc64 = true;
+          if (use_mg) {
+            // the FP64 finish keeps the FP32 hierarchy as its preconditioner
+            // (FGMRES is flexible): float V-cycles on the float linearisation
+            float *u32 = nullptr, *d32 = nullptr;
+            TRY(prepare<float>(m, U, Un, st, &u32, &d32));
+            if (m->mg->elem_size != (int)sizeof(float)) {
+              TRY(mg_build<float>(m, pcs, u32, d32, o.mg_omega, o.mg_smooth, st));
               tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
             } else {
-              TRY(mg_update_state<double>(m, ut_t, dl_t, st));
+              TRY(mg_update_state<float>(m, u32, d32, st));
             }
+            TRY(ws.p32a.ensure(sizeof(float) * n + 16));
+            TRY(ws.p32b.ensure(sizeof(float) * n + 16));
+            mg32.ut = u32;
+            mg32.dl = d32;
+            mg32.vin = ws.p32a.as<float>();
+            mg32.zout = ws.p32b.as<float>();
           } else if (!have_pc64) {  // promote the FP32 blocks (built by an earlier FP32 iteration or step)
             TRY(ws.binv64.ensure(sizeof(double) * nb));
             vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
@@ -738,7 +776,8 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
         } else if (use_mg) {
           TRY(mg_update_state<double>(m, ut_t, dl_t, st));
         }
-        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st));
+        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st,
+                           (mixed && use_mg) ? &mg32 : nullptr));
         if (mixed) ++its64;
       }
       tj.ms += tk.ms;
@@ -942,6 +981,7 @@ void chns_mesh_destroy(chns_mesh *m) {
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
   m->ws.e32.release(); m->ws.e64.release(); m->ws.ctr.release(); m->ws.count.release();
+  m->ws.Ublk.release(); m->ws.p32a.release(); m->ws.p32b.release();
   delete m;
   cudaSetDevice(prev);
 }
@@ -987,41 +1027,56 @@ chns_status chns_init_mu(const chns_mesh *mc, const chns_params *p, double *U, v
   const int nf = m->nf, imu = m->dim + 2;
   const int64_t n = m->n_nodes * nf;
   PhysCoef pc = make_coef(*p, m->lo, m->hi);
-  // M mu_new = M mu + F_mu(U; U), M = -2 (dF_mu / d mu_new); conjugate gradients
+  // M mu_new = M mu + F_mu(U; U), M = -2 (dF_mu / d mu_new): conjugate
+  // gradients preconditioned by the lumped mass (the row sums of M, from one
+  // J.w on the indicator of the mu field), which keeps the iteration count
+  // bounded however much the leaf sizes differ
   TRY(ws.F.ensure(sizeof(double) * n));
   TRY(ws.dU.ensure(sizeof(double) * n));
   TRY(ws.r.ensure(sizeof(double) * n));
-  TRY(ws.V.ensure(sizeof(double) * 2 * n));
-  double *r = ws.r.as<double>(), *x = ws.dU.as<double>(), *pv = ws.V.as<double>(), *q = pv + n;
+  TRY(ws.V.ensure(sizeof(double) * 4 * n));
+  double *r = ws.r.as<double>(), *x = ws.dU.as<double>(), *pv = ws.V.as<double>(), *q = pv + n, *d = pv + 2 * n,
+         *z = pv + 3 * n;
   double *ut = nullptr, *dl = nullptr;
   TRY(prepare<double>(m, U, U, st, &ut, &dl));
   TRY(residual_prepared(m, pc, U, ut, dl, nullptr, nullptr, r, st));
   vec_mask_field(r, m->n_nodes, nf, imu, 1.0, st);
+  // lumped mass: d = M 1 on the mu field (z holds the indicator of the mu field)
+  TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
+  TRY(ws.hdev.ensure(sizeof(double) * 8 * kHessSlot));
+  TRY(ensure_pinned(ws));
+  vec_fill_field(z, m->n_nodes, nf, imu, 1.0, st);
+  TRY(jacvec_prepared<double>(m, pc, ut, dl, z, d, st));
+  vec_mask_field(d, m->n_nodes, nf, imu, -2.0, st);
   CHNS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-  CHNS_CUDA_TRY(cudaMemcpyAsync(pv, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  double rr = 0.0;
-  TRY(norm2(m, r, &rr, st));
-  rr *= rr;
+  auto dot = [&](const double *a, const double *b, double *out) -> chns_status {
+    vec_dot(a, b, n, ws.red.as<double>(), ws.hdev.as<double>(), st);
+    CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, ws.hdev.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    CHNS_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = ws.hpinned[0];
+    return CHNS_OK;
+  };
+  vec_div_field(r, d, z, m->n_nodes, nf, imu, st);
+  CHNS_CUDA_TRY(cudaMemcpyAsync(pv, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double rz = 0.0, rr = 0.0;
+  TRY(dot(r, z, &rz));
+  TRY(dot(r, r, &rr));
   const double stop = 1e-26 * std::max(rr, 1e-300);
-  for (int it = 0; it < 10000 && rr > stop && rr > 0.0; ++it) {
+  for (int it = 0; it < 10000 && rr > stop && rz > 0.0; ++it) {
     TRY(jacvec_prepared<double>(m, pc, ut, dl, pv, q, st));
     vec_mask_field(q, m->n_nodes, nf, imu, -2.0, st);
     double pq = 0.0;
-    TRY(ws.red.ensure(sizeof(double) * (kMaxRestart + 16) * red_blocks()));
-    TRY(ws.hdev.ensure(sizeof(double) * 8 * kHessSlot));
-    vec_dot(pv, q, n, ws.red.as<double>(), ws.hdev.as<double>(), st);
-    CHNS_CUDA_TRY(cudaMemcpyAsync(ws.hpinned, ws.hdev.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, st));
-    CHNS_CUDA_TRY(cudaStreamSynchronize(st));
-    pq = ws.hpinned[0];
+    TRY(dot(pv, q, &pq));
     if (!(pq > 0.0)) { set_error("mass matrix not positive in CG"); return CHNS_ERR_KRYLOV; }
-    double a = rr / pq;
+    const double a = rz / pq;
     vec_axpby(a, pv, 1.0, x, n, st);
     vec_axpby(-a, q, 1.0, r, n, st);
-    double rn = 0.0;
-    TRY(norm2(m, r, &rn, st));
-    double rr2 = rn * rn;
-    vec_axpby(1.0, r, rr2 / rr, pv, n, st);
-    rr = rr2;
+    vec_div_field(r, d, z, m->n_nodes, nf, imu, st);
+    double rz2 = 0.0;
+    TRY(dot(r, z, &rz2));
+    TRY(dot(r, r, &rr));
+    vec_axpby(1.0, z, rz2 / rz, pv, n, st);
+    rz = rz2;
   }
   vec_axpby(1.0, x, 1.0, U, n, st);
   return check_launch();

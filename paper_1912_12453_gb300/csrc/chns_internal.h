@@ -60,6 +60,7 @@ struct Workspace {
   DevBuf ut, dl, ut32, dl32, f;        // prepared nodal fields (time averages / increments)
   DevBuf F, dU, r;                     // double n_dof
   DevBuf Ublk;                         // double n_dof: the previous block-iteration state
+  DevBuf p32a, p32b;                   // float n_dof: FP32 V-cycle input / output in the FP64 finish
   DevBuf V;                            // double (m+1) n_dof Krylov basis
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors
@@ -145,6 +146,7 @@ struct chns_mesh {
   void *coef32 = nullptr, *coef64 = nullptr;  // per-instance element coefficients (device)
   std::vector<int64_t> inst_node_start;      // n_inst + 1 (host)
   std::vector<int> inst_max_level;           // n_inst (host)
+  std::vector<const chns_mesh *> inst_meshes;  // union: the instance meshes (not owned)
   int64_t n_wall = 0;
   std::vector<int64_t> node_xyz;       // host: n_nodes * dim integer coordinates
   // device arrays

@@ -904,6 +904,19 @@ chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, c
   return CHNS_OK;
 }
 
+// the per-instance coefficient tables of src, copied to dst (same instances)
+chns_status copy_coef_tables(const chns_mesh *src, chns_mesh *dst) {
+  if (!src->coef32) { set_error("union mesh without coefficient tables"); return CHNS_ERR_ARG; }
+  const size_t n = (size_t)src->n_inst;
+  if (!dst->coef32) {
+    CHNS_CUDA_TRY(cudaMalloc(&dst->coef32, sizeof(KCoef<float>) * n));
+    CHNS_CUDA_TRY(cudaMalloc(&dst->coef64, sizeof(KCoef<double>) * n));
+  }
+  CHNS_CUDA_TRY(cudaMemcpy(dst->coef32, src->coef32, sizeof(KCoef<float>) * n, cudaMemcpyDeviceToDevice));
+  CHNS_CUDA_TRY(cudaMemcpy(dst->coef64, src->coef64, sizeof(KCoef<double>) * n, cudaMemcpyDeviceToDevice));
+  return CHNS_OK;
+}
+
 int64_t energy_blocks(const chns_mesh *m) { return (int64_t)grid_for(m->n_elem << m->dim); }
 
 void launch_energy(const chns_mesh *m, const PhysCoef &pc, const double *U, double *partial,

@@ -26,6 +26,7 @@ void launch_dirichlet_res(const chns_mesh *m, const double *Un, const double *bc
 int64_t energy_blocks(const chns_mesh *m);
 // per-instance element coefficients of a batched (union) mesh
 chns_status upload_coef_tables(chns_mesh *m, const std::vector<PhysCoef> &pcs, cudaStream_t st);
+chns_status copy_coef_tables(const chns_mesh *src, chns_mesh *dst);
 void launch_energy(const chns_mesh *m, const PhysCoef &pc, const double *U, double *partial, cudaStream_t st);
 
 }  // namespace chns

@@ -580,6 +580,11 @@ chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u) 
   }
   u->inst_node_start = node_off;
   u->inst_max_level.clear();
+  u->inst_meshes = ms;
+  // uniform when every instance is uniform at one level (a multigrid bottom)
+  u->uniform = true;
+  for (auto *m : ms)
+    if (!m->uniform || m->min_level != ms[0]->min_level) u->uniform = false;
   // elements colour by colour, instance by instance
   std::vector<int32_t> conn;
   std::vector<uint8_t> lev;

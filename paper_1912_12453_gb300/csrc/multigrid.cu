@@ -46,6 +46,7 @@ namespace chns {
 chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t *anchor, int max_level,
                        const double lo[3], const double hi[3], chns_mesh *m);
 chns_status build_gather(chns_mesh *m);
+chns_status build_union(const std::vector<const chns_mesh *> &ms, chns_mesh *u);
 
 namespace {
 
@@ -200,8 +201,15 @@ std::vector<Leaf> coarsen(const std::vector<Leaf> &in, int dim, int max_level, i
   return out;
 }
 
-// P (coarse -> fine nodes) and its transpose, and the injection coarse -> fine
-chns_status build_transfer(const chns_mesh *F, const chns_mesh *C, MgLevel &L) {
+// Host lists of one problem instance: P (coarse -> fine nodes) as pptr
+// (n_fine + 1), pcol, pw; the injection coarse node -> fine node at its
+// position.  Local node numbers of F and C.
+struct TransferLists {
+  std::vector<int32_t> pptr, pcol, inj;
+  std::vector<float> pw;
+};
+
+chns_status transfer_lists(const chns_mesh *F, const chns_mesh *C, TransferLists &T) {
   const int dim = F->dim, nc = 1 << dim;
   const int ml = F->max_level;
   const int64_t top = int64_t(1) << ml;
@@ -285,18 +293,6 @@ chns_status build_transfer(const chns_mesh *F, const chns_mesh *C, MgLevel &L) {
     }
     pptr[i + 1] = (int32_t)pcol.size();
   }
-  // restriction = transpose, lists in increasing fine node order
-  std::vector<int32_t> rptr(size_t(C->n_nodes) + 1, 0);
-  for (int32_t j : pcol) rptr[size_t(j) + 1]++;
-  for (int64_t j = 0; j < C->n_nodes; ++j) rptr[j + 1] += rptr[j];
-  std::vector<int32_t> rcol(pcol.size()), fill(rptr.begin(), rptr.end() - 1);
-  std::vector<float> rw(pcol.size());
-  for (int64_t i = 0; i < F->n_nodes; ++i)
-    for (int32_t e = pptr[i]; e < pptr[i + 1]; ++e) {
-      const int32_t j = pcol[e];
-      rcol[fill[j]] = (int32_t)i;
-      rw[fill[j]++] = pw[e];
-    }
   // injection: coarse node j -> the fine node at its position
   KeyMap fnode(size_t(F->n_nodes) + 16);
   for (int64_t i = 0; i < F->n_nodes; ++i) fnode.insert(pack(&F->node_xyz[i * dim], dim), i);
@@ -306,6 +302,54 @@ chns_status build_transfer(const chns_mesh *F, const chns_mesh *C, MgLevel &L) {
     if (i < 0) { set_error("multigrid: coarse node %lld is not a fine node", (long long)j); return CHNS_ERR_MESH; }
     inj[j] = (int32_t)i;
   }
+  T.pptr.swap(pptr);
+  T.pcol.swap(pcol);
+  T.pw.swap(pw);
+  T.inj.swap(inj);
+  return CHNS_OK;
+}
+
+// identity lists of an instance that is already at the bottom level
+void identity_lists(int64_t n, TransferLists &T) {
+  T.pptr.resize(n + 1);
+  T.pcol.resize(n);
+  T.pw.assign(n, 1.0f);
+  T.inj.resize(n);
+  for (int64_t i = 0; i <= n; ++i) T.pptr[i] = (int32_t)i;
+  for (int64_t i = 0; i < n; ++i) T.pcol[i] = T.inj[i] = (int32_t)i;
+}
+
+// concatenate the instances' lists (node offsets of the fine and coarse
+// union levels), form the restriction P^T (lists in increasing fine node
+// order) and upload
+chns_status upload_transfer(const std::vector<TransferLists> &parts, const std::vector<int64_t> &foff,
+                            const std::vector<int64_t> &coff, MgLevel &L) {
+  const int64_t nfine = foff.back(), ncoarse = coff.back();
+  std::vector<int32_t> pptr(size_t(nfine) + 1, 0), pcol;
+  std::vector<int32_t> inj(static_cast<size_t>(ncoarse), 0);
+  std::vector<float> pw;
+  for (size_t q = 0; q < parts.size(); ++q) {
+    const TransferLists &T = parts[q];
+    for (int64_t i = 0; i + 1 < (int64_t)T.pptr.size(); ++i) {
+      for (int32_t e = T.pptr[i]; e < T.pptr[i + 1]; ++e) {
+        pcol.push_back(int32_t(T.pcol[e] + coff[q]));
+        pw.push_back(T.pw[e]);
+      }
+      pptr[size_t(foff[q] + i) + 1] = (int32_t)pcol.size();
+    }
+    for (size_t j = 0; j < T.inj.size(); ++j) inj[coff[q] + j] = int32_t(T.inj[j] + foff[q]);
+  }
+  std::vector<int32_t> rptr(size_t(ncoarse) + 1, 0);
+  for (int32_t j : pcol) rptr[size_t(j) + 1]++;
+  for (int64_t j = 0; j < ncoarse; ++j) rptr[j + 1] += rptr[j];
+  std::vector<int32_t> rcol(pcol.size()), fill(rptr.begin(), rptr.end() - 1);
+  std::vector<float> rw(pcol.size());
+  for (int64_t i = 0; i < nfine; ++i)
+    for (int32_t e = pptr[i]; e < pptr[i + 1]; ++e) {
+      const int32_t j = pcol[e];
+      rcol[fill[j]] = (int32_t)i;
+      rw[fill[j]++] = pw[e];
+    }
   TRY_MG(upload(&L.pptr, pptr));
   TRY_MG(upload(&L.pcol, pcol));
   TRY_MG(upload(&L.pw, pw));
@@ -314,6 +358,32 @@ chns_status build_transfer(const chns_mesh *F, const chns_mesh *C, MgLevel &L) {
   TRY_MG(upload(&L.rw, rw));
   TRY_MG(upload(&L.inj, inj));
   L.nnz = (int64_t)pcol.size();
+  return CHNS_OK;
+}
+
+// one level coarser: every family of leaves at the mesh's finest leaf level
+// merged (nullptr with CHNS_OK when the mesh is already at or below `bottom`)
+chns_status coarser_mesh(const chns_mesh *m, int bottom, chns_mesh **out) {
+  *out = nullptr;
+  std::vector<Leaf> cur = mesh_leaves(m);
+  int lmax = 0;
+  for (const Leaf &l : cur) lmax = std::max<int>(lmax, l.level);
+  if (lmax <= bottom) return CHNS_OK;
+  std::vector<Leaf> nxt = coarsen(cur, m->dim, m->max_level, lmax);
+  std::vector<uint8_t> lev(nxt.size());
+  std::vector<uint32_t> anc(nxt.size() * m->dim);
+  for (size_t e = 0; e < nxt.size(); ++e) {
+    lev[e] = nxt[e].level;
+    for (int d = 0; d < m->dim; ++d) anc[e * m->dim + d] = nxt[e].a[d];
+  }
+  chns_mesh *c = new chns_mesh;
+  chns_status s = build_mesh(m->dim, (int64_t)nxt.size(), lev.data(), anc.data(), m->max_level, m->lo, m->hi, c);
+  if (s == CHNS_OK) s = build_gather(c);
+  if (s != CHNS_OK) {
+    chns_mesh_destroy(c);
+    return s;
+  }
+  *out = c;
   return CHNS_OK;
 }
 
@@ -337,8 +407,12 @@ void mg_release(Multigrid *g) {
 }
 
 chns_status mg_setup(chns_mesh *m, int bottom) {
-  if (m->n_inst != 1) { set_error("multigrid: batched (union) meshes use the two-level preconditioner"); return CHNS_ERR_ARG; }
-  bottom = std::max(1, std::min(bottom, m->min_level));
+  // instances: the mesh itself, or the problem instances of a batch union
+  std::vector<const chns_mesh *> inst = m->n_inst > 1 ? m->inst_meshes : std::vector<const chns_mesh *>{m};
+  if ((int)inst.size() != m->n_inst) { set_error("multigrid: union mesh without its instance meshes"); return CHNS_ERR_ARG; }
+  int minl = 64;
+  for (const chns_mesh *q : inst) minl = std::min(minl, q->min_level);
+  bottom = std::max(1, std::min(bottom, minl));
   if (m->mg && m->mg->bottom_level == bottom) return CHNS_OK;
   mg_release(m->mg);
   m->mg = new Multigrid;
@@ -346,35 +420,72 @@ chns_status mg_setup(chns_mesh *m, int bottom) {
   G.bottom_level = bottom;
   G.lv.resize(1);
   G.lv[0].mesh = m;
-  std::vector<Leaf> cur = mesh_leaves(m);
-  chns_mesh *prev = m;
-  while (true) {
-    int lmax = 0;
-    for (const Leaf &l : cur) lmax = std::max<int>(lmax, l.level);
-    if (lmax <= bottom) break;
-    std::vector<Leaf> nxt = coarsen(cur, m->dim, m->max_level, lmax);
-    std::vector<uint8_t> lev(nxt.size());
-    std::vector<uint32_t> anc(nxt.size() * m->dim);
-    for (size_t e = 0; e < nxt.size(); ++e) {
-      lev[e] = nxt[e].level;
-      for (int d = 0; d < m->dim; ++d) anc[e * m->dim + d] = nxt[e].a[d];
+  // per instance: its meshes level by level (level 0 not owned)
+  const size_t ni = inst.size();
+  std::vector<std::vector<chns_mesh *>> chain(ni);
+  std::vector<size_t> owned;  // chain[0] entries already owned by a level
+  auto release_chains = [&]() {
+    for (auto &c : chain)
+      for (size_t l = 1; l < c.size(); ++l)
+        if (c[l]) chns_mesh_destroy(c[l]);
+    chain.clear();
+  };
+  auto fail = [&](chns_status s) {
+    for (size_t l : owned) chain[0][l] = nullptr;
+    release_chains();
+    mg_release(m->mg);
+    m->mg = nullptr;
+    return s;
+  };
+  size_t depth = 0;
+  for (size_t q = 0; q < ni; ++q) {
+    chain[q].push_back(const_cast<chns_mesh *>(inst[q]));
+    while (true) {
+      chns_mesh *c = nullptr;
+      chns_status s = coarser_mesh(chain[q].back(), bottom, &c);
+      if (s != CHNS_OK) return fail(s);
+      if (!c) break;
+      chain[q].push_back(c);
     }
+    depth = std::max(depth, chain[q].size() - 1);
+  }
+  // single instance: the chain's coarse meshes become the levels' meshes
+  // (ownership moves to the level as it is pushed); a union: each level is
+  // the union of the instances' meshes of that level (an instance already at
+  // the bottom repeats its bottom mesh, with identity transfers)
+  for (size_t l = 1; l <= depth; ++l) {
     MgLevel L;
-    L.mesh = new chns_mesh;
-    chns_status s = build_mesh(m->dim, (int64_t)nxt.size(), lev.data(), anc.data(), m->max_level, m->lo, m->hi,
-                               L.mesh);
-    if (s == CHNS_OK) s = build_gather(L.mesh);
-    if (s == CHNS_OK) s = build_transfer(prev, L.mesh, L);
+    std::vector<const chns_mesh *> ms(ni);
+    std::vector<TransferLists> parts(ni);
+    for (size_t q = 0; q < ni; ++q) {
+      const size_t lf = std::min(l - 1, chain[q].size() - 1), lc = std::min(l, chain[q].size() - 1);
+      ms[q] = chain[q][lc];
+      chns_status s = CHNS_OK;
+      if (lf == lc) identity_lists(chain[q][lc]->n_nodes, parts[q]);
+      else s = transfer_lists(chain[q][lf], chain[q][lc], parts[q]);
+      if (s != CHNS_OK) return fail(s);
+    }
+    chns_status s = CHNS_OK;
+    if (ni == 1) {
+      L.mesh = chain[0][l];
+    } else {
+      L.mesh = new chns_mesh;
+      s = build_union(ms, L.mesh);
+      if (s == CHNS_OK) s = build_gather(L.mesh);
+      if (s == CHNS_OK) s = copy_coef_tables(m, L.mesh);
+    }
+    const chns_mesh *F = G.lv[l - 1].mesh;
+    if (s == CHNS_OK) s = upload_transfer(parts, F->inst_node_start, L.mesh->inst_node_start, L);
     if (s != CHNS_OK) {
+      if (ni == 1) L.mesh = nullptr;  // still owned by the chain
       free_level(L, true);
-      mg_release(m->mg);
-      m->mg = nullptr;
-      return s;
+      return fail(s);
     }
     G.lv.push_back(L);
-    prev = G.lv.back().mesh;
-    cur.swap(nxt);
+    if (ni == 1) owned.push_back(l);
   }
+  for (size_t l : owned) chain[0][l] = nullptr;  // now owned by the levels
+  release_chains();
   // the bottom level is solved exactly: coarse grid = the bottom mesh itself
   chns_mesh *b = G.lv.back().mesh;
   if (!b->uniform || b->min_level != bottom) {

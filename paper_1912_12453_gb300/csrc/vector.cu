@@ -307,6 +307,19 @@ __global__ void k_max_partials(const double *__restrict__ partial, int nb, doubl
   }
 }
 
+// field k of each node block = v, the others 0
+__global__ void k_fill_field(double *__restrict__ y, int64_t n_nodes, int nf, int k, double v) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n_nodes * nf; t += int64_t(gridDim.x) * kB)
+    y[t] = (t % nf == k) ? v : 0.0;
+}
+
+// z = r / d in field k of each node block (d > 0 there), 0 in the others
+__global__ void k_div_field(const double *__restrict__ r, const double *__restrict__ d, double *__restrict__ z,
+                            int64_t n_nodes, int nf, int k) {
+  for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n_nodes * nf; t += int64_t(gridDim.x) * kB)
+    z[t] = (t % nf == k && d[t] > 0.0) ? r[t] / d[t] : 0.0;
+}
+
 // keep field k of each node block, scaled; zero the others
 __global__ void k_mask_field(double *__restrict__ y, int64_t n_nodes, int nf, int k, double s) {
   for (int64_t t = blockIdx.x * int64_t(kB) + threadIdx.x; t < n_nodes * nf; t += int64_t(gridDim.x) * kB)
@@ -466,6 +479,16 @@ void vec_maxabs_diff(const double *x, const double *y, int64_t n, double *partia
   k_maxabs_diff<<<kRedBlocks, kB, 0, st>>>(x, y, n, partial);
   k_max_partials<<<1, kB, 0, st>>>(partial, kRedBlocks, res);
   note_launches(2);
+}
+
+void vec_fill_field(double *y, int64_t n_nodes, int nf, int k, double v, cudaStream_t st) {
+  k_fill_field<<<grid_n(n_nodes * nf), kB, 0, st>>>(y, n_nodes, nf, k, v);
+  note_launches(1);
+}
+
+void vec_div_field(const double *r, const double *d, double *z, int64_t n_nodes, int nf, int k, cudaStream_t st) {
+  k_div_field<<<grid_n(n_nodes * nf), kB, 0, st>>>(r, d, z, n_nodes, nf, k);
+  note_launches(1);
 }
 
 void vec_mask_field(double *y, int64_t n_nodes, int nf, int k, double s, cudaStream_t st) {

@@ -39,6 +39,10 @@ void vec_combine(const T *Z, int64_t ld, int nz, const double *c, double *x, int
 void vec_axpby(double a, const double *x, double b, double *y, int64_t n, cudaStream_t st);
 void vec_lincomb(double a, const double *x, double b, const double *y, double *z, int64_t n, cudaStream_t st);
 void vec_mask_field(double *y, int64_t n_nodes, int nf, int k, double s, cudaStream_t st);
+// field k = v, the other fields 0
+void vec_fill_field(double *y, int64_t n_nodes, int nf, int k, double v, cudaStream_t st);
+// z = r / d in field k (where d > 0), 0 elsewhere
+void vec_div_field(const double *r, const double *d, double *z, int64_t n_nodes, int nf, int k, cudaStream_t st);
 // zero the fields whose bit in fmask is clear
 void vec_mask_fields(double *y, int64_t n_nodes, int nf, uint32_t fmask, cudaStream_t st);
 // *res = max_i |x_i - y_i| (partial: red_blocks() doubles)

