@@ -305,18 +305,10 @@ bool inject_krylov_fault() {
 // stream before the host waits for column j (two result slots, a pinned
 // mirror each): the GPU never idles on the host.  When step j converges,
 // the queued step j + 1 is discarded.
-// The FP32 multigrid hierarchy used as the preconditioner of a double
-// FGMRES (the FP64 finish of the mixed path): the V-cycle runs in float on
-// the float linearisation (ut32, dl32), between conversions of v and z.
-struct Mg32 {
-  const float *ut = nullptr, *dl = nullptr;
-  float *vin = nullptr, *zout = nullptr;
-};
-
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
                    bool mg, const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
-                   cudaStream_t st, const Mg32 *mg32 = nullptr) {
+                   cudaStream_t st) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
@@ -361,12 +353,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     double *h1 = hd + 3 * K * sl, *h2 = h1 + K, *nr = h1 + 2 * K;
     T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
     T *zj = Z + (int64_t)j * ld;
-    if (mg32) {
-      const int64_t nn = m->n_nodes * m->nf;
-      vec_convert<T, float>(vj, mg32->vin, nn, 1.0, s);
-      TRY(mg_apply<float>(m, pc, mg32->ut, mg32->dl, mg32->vin, mg32->zout, s));
-      vec_convert<float, T>(mg32->zout, zj, nn, 1.0, s);
-    } else if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
+    if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
     else precond_apply<T>(m, Binv, coarse, vj, zj, s);
     int ev = 0;
     if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j], s, cudaEventRecordExternal));
@@ -396,7 +383,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
     key.p[14] = ctr; key.p[15] = mg ? m->mg : nullptr;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
-    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph + 2 * (mg32 != nullptr);
+    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph;
     key.i[7] = m->jv_variant;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
@@ -599,7 +586,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
   bool have_pc = ws.pc_steps_left > 0 && ws.pc_precision == (int)o.precision && ws.pc_coarse == Lc &&
                  ws.pc_kind == (int)o.preconditioner && ws.pc_smooth == o.mg_smooth && ws.pc_omega == o.mg_omega &&
                  std::memcmp(&ws.pc_params, p, sizeof(chns_params)) == 0 && o.reuse_preconditioner > 0 &&
-                 (!use_mg || m->mg->ready);
+                 (!use_mg || m->mg->ready[mixed ? 0 : 1]);
   if (have_pc) --ws.pc_steps_left;
   auto mark_built = [&]() {
     ws.pc_precision = (int)o.precision;
@@ -722,7 +709,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
         float *ut_t = nullptr, *dl_t = nullptr;
         TRY(prepare<float>(m, U, Un, st, &ut_t, &dl_t));
         if (o.autotune && !m->jv_tuned) TRY(autotune_jacvec(m, pcs, ut_t, dl_t, st));
-        if (!have_pc || !o.reuse_preconditioner || (use_mg && m->mg->elem_size != (int)sizeof(float))) {
+        if (!have_pc || !o.reuse_preconditioner || (use_mg && !m->mg->ready[0])) {
           if (use_mg) {
             TRY(mg_build<float>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
           } else {
@@ -739,31 +726,25 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
       } else {
         double *ut_t = nullptr, *dl_t = nullptr;
         TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
-        Mg32 mg32;
         if (mixed) {
           if (use_mg) {
-            // the FP64 finish keeps the FP32 hierarchy as its preconditioner
-            // (FGMRES is flexible): float V-cycles on the float linearisation
-            float *u32 = nullptr, *d32 = nullptr;
-            TRY(prepare<float>(m, U, Un, st, &u32, &d32));
-            if (m->mg->elem_size != (int)sizeof(float)) {
-              TRY(mg_build<float>(m, pcs, u32, d32, o.mg_omega, o.mg_smooth, st));
+            // the FP64 finish: V-cycles with operators and smoother blocks
+            // probed in double (the weakly determined modes it must resolve
+            // are where float probes fall short: on the 7M-leaf mesh float
+            // blocks, promoted, left FGMRES at its iteration cap); built once
+            // and kept next to the float ones until the next float build
+            if (!m->mg->ready[1]) {
+              TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st, true));
               tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
             } else {
-              TRY(mg_update_state<float>(m, u32, d32, st));
+              TRY(mg_update_state<double>(m, ut_t, dl_t, st));
             }
-            TRY(ws.p32a.ensure(sizeof(float) * n + 16));
-            TRY(ws.p32b.ensure(sizeof(float) * n + 16));
-            mg32.ut = u32;
-            mg32.dl = d32;
-            mg32.vin = ws.p32a.as<float>();
-            mg32.zout = ws.p32b.as<float>();
           } else if (!have_pc64) {  // promote the FP32 blocks (built by an earlier FP32 iteration or step)
             TRY(ws.binv64.ensure(sizeof(double) * nb));
             vec_convert<float, double>(ws.binv.as<float>(), ws.binv64.as<double>(), nb, 1.0, st);
             have_pc64 = true;
           }
-        } else if (!have_pc || !o.reuse_preconditioner || (use_mg && m->mg->elem_size != (int)sizeof(double))) {
+        } else if (!have_pc || !o.reuse_preconditioner || (use_mg && !m->mg->ready[1])) {
           if (use_mg) {
             TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st));
           } else {
@@ -776,8 +757,7 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
         } else if (use_mg) {
           TRY(mg_update_state<double>(m, ut_t, dl_t, st));
         }
-        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st,
-                           (mixed && use_mg) ? &mg32 : nullptr));
+        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st));
         if (mixed) ++its64;
       }
       tj.ms += tk.ms;
@@ -981,7 +961,7 @@ void chns_mesh_destroy(chns_mesh *m) {
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
   m->ws.e32.release(); m->ws.e64.release(); m->ws.ctr.release(); m->ws.count.release();
-  m->ws.Ublk.release(); m->ws.p32a.release(); m->ws.p32b.release();
+  m->ws.Ublk.release();
   delete m;
   cudaSetDevice(prev);
 }

@@ -105,22 +105,34 @@ __global__ void __launch_bounds__(kB) k_smooth(int64_t n, const T *__restrict__ 
 }
 
 // bc[j] = sum over the restriction list of coarse node j of w (b - y)[i];
-// zero in the constrained rows of the coarse level
+// zero in the constrained rows of the coarse level.  Eight lanes per coarse
+// node (lane s takes the list entries s, s + 8, ...), then a fixed xor
+// butterfly over the eight lanes: deterministic, and eight times the
+// parallelism of a thread per coarse node on these short scattered lists.
+constexpr int kRLanes = 8;
 template <typename T, int NF>
 __global__ void __launch_bounds__(kB) k_restrict_res(int64_t nc, int dim, const int32_t *__restrict__ rptr,
                                                      const int32_t *__restrict__ rcol, const float *__restrict__ rw,
                                                      const T *__restrict__ b, const T *__restrict__ y,
                                                      const uint8_t *__restrict__ cflag, T *__restrict__ bc) {
-  for (int64_t j = blockIdx.x * int64_t(kB) + threadIdx.x; j < nc; j += int64_t(gridDim.x) * kB) {
-    T acc[NF];
+  const int64_t j = (blockIdx.x * int64_t(kB) + threadIdx.x) / kRLanes;
+  const int sub = threadIdx.x % kRLanes;
+  T acc[NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) acc[k] = T(0);
-    for (int e = rptr[j]; e < rptr[j + 1]; ++e) {
+  for (int k = 0; k < NF; ++k) acc[k] = T(0);
+  if (j < nc) {
+    for (int e = rptr[j] + sub; e < rptr[j + 1]; e += kRLanes) {
       const int64_t i = rcol[e];
       const T w = T(rw[e]);
 #pragma unroll
       for (int k = 0; k < NF; ++k) acc[k] = fma(w, b[i * NF + k] - y[i * NF + k], acc[k]);
     }
+  }
+#pragma unroll
+  for (int k = 0; k < NF; ++k)
+#pragma unroll
+    for (int o = kRLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (j < nc && sub == 0) {
     const uint8_t fl = cflag[j];
     if (fl & 1)
       for (int k = 0; k < dim; ++k) acc[k] = T(0);
@@ -393,7 +405,12 @@ void free_level(MgLevel &L, bool own_mesh) {
   cudaFree(L.inj);
   L.pptr = L.pcol = L.rptr = L.rcol = L.inj = nullptr;
   L.pw = L.rw = nullptr;
-  L.ut.release(); L.dl.release(); L.binv.release(); L.x.release(); L.b.release(); L.y.release();
+  for (int k = 0; k < 2; ++k) {
+    L.ut[k].release();
+    L.dl[k].release();
+    L.binv[k].release();
+  }
+  L.x.release(); L.b.release(); L.y.release();
   if (own_mesh && L.mesh) chns_mesh_destroy(L.mesh);
   L.mesh = nullptr;
 }
@@ -530,44 +547,51 @@ static chns_status jv_level(void *ctx, const T *w, T *y) {
 }
 
 template <typename T>
+constexpr int prec_index() { return sizeof(T) == 8 ? 1 : 0; }
+
+template <typename T>
 chns_status mg_update_state(chns_mesh *m, const T *ut0, const T *dl0, cudaStream_t st) {
   Multigrid &G = *m->mg;
+  constexpr int P = prec_index<T>();
   const T *uf = ut0, *df = dl0;
   for (size_t l = 1; l < G.lv.size(); ++l) {
     MgLevel &L = G.lv[l];
     chns_mesh *c = L.mesh;
-    TRY_MG(L.ut.ensure(sizeof(T) * c->n_nodes * c->nf));
-    TRY_MG(L.dl.ensure(sizeof(T) * c->n_nodes * (c->dim + 1)));
-    launch_inject<T>(c, L.inj, uf, df, L.ut.as<T>(), L.dl.as<T>(), st);
-    uf = L.ut.as<T>();
-    df = L.dl.as<T>();
+    TRY_MG(L.ut[P].ensure(sizeof(T) * c->n_nodes * c->nf));
+    TRY_MG(L.dl[P].ensure(sizeof(T) * c->n_nodes * (c->dim + 1)));
+    launch_inject<T>(c, L.inj, uf, df, L.ut[P].as<T>(), L.dl[P].as<T>(), st);
+    uf = L.ut[P].as<T>();
+    df = L.dl[P].as<T>();
   }
   return check_launch();
 }
 
 template <typename T>
 chns_status mg_build(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl0, double omega, int smooth,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool keep_other) {
   Multigrid &G = *m->mg;
+  constexpr int P = prec_index<T>();
   G.omega = omega;
   G.smooth = smooth;
+  G.ready[P] = false;
+  if (!keep_other) G.ready[1 - P] = false;
   TRY_MG(mg_update_state<T>(m, ut0, dl0, st));
   const size_t nl = G.lv.size();
   for (size_t l = 0; l < nl; ++l) {
     MgLevel &L = G.lv[l];
     chns_mesh *c = L.mesh;
-    const T *ut = l == 0 ? ut0 : L.ut.as<T>();
-    const T *dl = l == 0 ? dl0 : L.dl.as<T>();
+    const T *ut = l == 0 ? ut0 : L.ut[P].as<T>();
+    const T *dl = l == 0 ? dl0 : L.dl[P].as<T>();
     const int64_t n = c->n_nodes * c->nf;
-    TRY_MG(L.x.ensure(sizeof(T) * n + 16));
-    TRY_MG(L.b.ensure(sizeof(T) * n + 16));
-    TRY_MG(L.y.ensure(sizeof(T) * n + 16));
+    TRY_MG(L.x.ensure(sizeof(double) * n + 16));
+    TRY_MG(L.b.ensure(sizeof(double) * n + 16));
+    TRY_MG(L.y.ensure(sizeof(double) * n + 16));
     T *E = nullptr;
     TRY_MG(ensure_ebuf<T>(c, &E));  // before any graph capture: nothing allocates inside a V-cycle
     if (sizeof(T) == sizeof(float) && G.autotune && l > 0 && !c->jv_tuned)
       TRY_MG(autotune_jacvec(c, pc, reinterpret_cast<const float *>(ut), reinterpret_cast<const float *>(dl), st));
     if (l + 1 < nl) {
-      TRY_MG(build_block_jacobi<T>(c, pc, ut, dl, L.binv, st, omega));
+      TRY_MG(build_block_jacobi<T>(c, pc, ut, dl, L.binv[P], st, omega));
     } else {
       // bottom: dense inverse of the level's own operator (coarse grid = this mesh)
       TRY_MG(c->ws.wv.ensure(sizeof(T) * n));
@@ -576,8 +600,7 @@ chns_status mg_build(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl
       TRY_MG(coarse_build<T>(c, &jv_level<T>, &ctx, c->ws.wv.as<T>(), c->ws.yv.as<T>(), st));
     }
   }
-  G.elem_size = (int)sizeof(T);
-  G.ready = true;
+  G.ready[P] = true;
   ++G.generation;
   return check_launch();
 }
@@ -590,11 +613,12 @@ chns_status mg_apply(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl
   const int nu = std::max(1, G.smooth);
   auto X = [&](int l) -> T * { return l == 0 ? z : G.lv[l].x.as<T>(); };
   auto B = [&](int l) -> const T * { return l == 0 ? v : G.lv[l].b.as<T>(); };
-  auto UT = [&](int l) -> const T * { return l == 0 ? ut0 : G.lv[l].ut.as<T>(); };
-  auto DL = [&](int l) -> const T * { return l == 0 ? dl0 : G.lv[l].dl.as<T>(); };
+  constexpr int P = prec_index<T>();
+  auto UT = [&](int l) -> const T * { return l == 0 ? ut0 : G.lv[l].ut[P].as<T>(); };
+  auto DL = [&](int l) -> const T * { return l == 0 ? dl0 : G.lv[l].dl[P].as<T>(); };
   auto smooth_k = [&](int l, const T *y) {
     chns_mesh *c = G.lv[l].mesh;
-    const T *Bi = G.lv[l].binv.as<T>();
+    const T *Bi = G.lv[l].binv[P].as<T>();
     if (c->nf == 5) k_smooth<T, 5><<<grid_n(c->n_nodes), kB, 0, st>>>(c->n_nodes, Bi, B(l), y, X(l));
     else k_smooth<T, 6><<<grid_n(c->n_nodes), kB, 0, st>>>(c->n_nodes, Bi, B(l), y, X(l));
     note_launches(1);
@@ -612,12 +636,11 @@ chns_status mg_apply(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl
     const MgLevel &Lc = G.lv[l + 1];
     chns_mesh *cc = Lc.mesh;
     T *bc = G.lv[l + 1].b.as<T>();
+    const unsigned gr = (unsigned)((cc->n_nodes * kRLanes + kB - 1) / kB);  // every coarse node one pass
     if (c->nf == 5)
-      k_restrict_res<T, 5><<<grid_n(cc->n_nodes), kB, 0, st>>>(cc->n_nodes, c->dim, Lc.rptr, Lc.rcol, Lc.rw, B(l), y,
-                                                               cc->nflag, bc);
+      k_restrict_res<T, 5><<<gr, kB, 0, st>>>(cc->n_nodes, c->dim, Lc.rptr, Lc.rcol, Lc.rw, B(l), y, cc->nflag, bc);
     else
-      k_restrict_res<T, 6><<<grid_n(cc->n_nodes), kB, 0, st>>>(cc->n_nodes, c->dim, Lc.rptr, Lc.rcol, Lc.rw, B(l), y,
-                                                               cc->nflag, bc);
+      k_restrict_res<T, 6><<<gr, kB, 0, st>>>(cc->n_nodes, c->dim, Lc.rptr, Lc.rcol, Lc.rw, B(l), y, cc->nflag, bc);
     note_launches(1);
   }
   // bottom: exact solve
@@ -645,9 +668,9 @@ chns_status mg_apply(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl
 template chns_status mg_update_state<float>(chns_mesh *, const float *, const float *, cudaStream_t);
 template chns_status mg_update_state<double>(chns_mesh *, const double *, const double *, cudaStream_t);
 template chns_status mg_build<float>(chns_mesh *, const PhysCoef &, const float *, const float *, double, int,
-                                     cudaStream_t);
+                                     cudaStream_t, bool);
 template chns_status mg_build<double>(chns_mesh *, const PhysCoef &, const double *, const double *, double, int,
-                                      cudaStream_t);
+                                      cudaStream_t, bool);
 template chns_status mg_apply<float>(chns_mesh *, const PhysCoef &, const float *, const float *, const float *,
                                      float *, cudaStream_t);
 template chns_status mg_apply<double>(chns_mesh *, const PhysCoef &, const double *, const double *, const double *,

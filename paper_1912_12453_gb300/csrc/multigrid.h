@@ -19,16 +19,15 @@ struct MgLevel {
   float *rw = nullptr;                       // ... and weights (restriction P_l^T)
   int32_t *inj = nullptr;                    // per node of level l: the level-(l-1) node at its position
   int64_t nnz = 0;
-  DevBuf ut, dl;                             // injected linearisation state (l >= 1)
-  DevBuf binv;                               // omega * inverse nodal diagonal blocks
-  DevBuf x, b, y;                            // V-cycle vectors
+  DevBuf ut[2], dl[2];                       // injected linearisation state (l >= 1), [float, double]
+  DevBuf binv[2];                            // omega * inverse nodal diagonal blocks, [float, double]
+  DevBuf x, b, y;                            // V-cycle vectors (sized for double)
 };
 
 struct Multigrid {
   std::vector<MgLevel> lv;
   int bottom_level = -1;                     // uniform octree level of the coarsest mesh
-  int elem_size = 0;                         // precision the operators were built in
-  bool ready = false;
+  bool ready[2] = {false, false};            // smoothers and bottom inverse built: [float, double]
   double omega = 0.7;
   int smooth = 1;
   uint64_t generation = 0;                   // bumped at every build (graph keys)
@@ -41,10 +40,11 @@ chns_status mg_setup(chns_mesh *m, int bottom);
 // inject the fine linearisation (ut0, dl0) down the levels
 template <typename T>
 chns_status mg_update_state(chns_mesh *m, const T *ut0, const T *dl0, cudaStream_t st);
-// injected states, damped block-Jacobi smoothers, bottom dense inverse
+// injected states, damped block-Jacobi smoothers, bottom dense inverse in
+// precision T; keep_other: the other precision's operators stay valid
 template <typename T>
 chns_status mg_build(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl0, double omega, int smooth,
-                     cudaStream_t st);
+                     cudaStream_t st, bool keep_other = false);
 // z = V-cycle(v): allocates nothing, so it can be captured into a graph
 template <typename T>
 chns_status mg_apply(chns_mesh *m, const PhysCoef &pc, const T *ut0, const T *dl0, const T *v, T *z,

@@ -275,3 +275,35 @@ def test_workload_applies_match_oracle(name):
     gotj32 = chns.jacvec(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32),
                          precision="fp32")
     assert rel(p.to_oracle(gotj32), refj) <= TOL32
+
+
+@pytest.fixture(scope="module")
+def largest():
+    import os
+    wl = W.workload("merge3d_l6_10")
+    p = Pair(wl.leaves)
+    Uo, Un = physical_state(p.om, wl)
+    w = W.perturbation(p.om.n_nodes, p.nf, 2)[1]
+    refj = p.om.jacvec_threads(wl.params, Un, Uo, w, os.cpu_count() or 1)
+    return wl, p, Uo, Un, w, refj
+
+
+@pytest.mark.parametrize("schedule", [0, 5, 6])
+def test_largest_workload_applies_match_oracle(largest, schedule):
+    """The largest workload (two merging droplets, octree levels 6-10, 6.98M
+    leaves, 771k hanging nodes, 39.6M DoF): FP64 and FP32-bulk J.w at the
+    initial state plus a seeded perturbation, every entry compared with the
+    oracle's J.w (run on all host cores), for the default FP32 schedule and
+    the two register budgets the autotuner picks on the uniform workload."""
+    import torch
+    from paper_1912_12453_gb300 import chns
+    wl, p, Uo, Un, w, refj = largest
+    assert p.gm.n_hanging == p.om.n_hanging and p.gm.n_nodes == p.om.n_nodes
+    if schedule == 0:
+        gotj = chns.jacvec(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w))
+        assert rel(p.to_oracle(gotj), refj) <= TOL64
+    p.gm.jacvec_schedule(schedule)
+    gotj32 = chns.jacvec(p.gm, wl.params, p.to_gpu(Un), p.to_gpu(Uo), p.to_gpu(w, torch.float32),
+                         precision="fp32")
+    assert rel(p.to_oracle(gotj32), refj) <= TOL32
+

@@ -68,6 +68,13 @@ def test_invalid_arguments_rejected_on_host(L):
     s, msg = _create(L, 4, [1], [[0, 0]], 1)
     assert s == 1 and "dim" in msg
     assert L.chns_mesh_info(None, None, None, None, None) == 1
+    # an empty leaf list, and a leaf level beyond max_level
+    s, msg = _create(L, 2, np.zeros(0, dtype=np.uint8), np.zeros((0, 2), dtype=np.uint32), 2)
+    assert s == 1 and "no leaves" in msg
+    s, msg = _create(L, 2, [3], [[0, 0]], 2)
+    assert s == 2
+    assert L.chns_mesh_check(None) == 1
+    assert L.chns_mesh_jacvec_schedule(None, 0, None, None) == 1
 
 
 def test_unsorted_leaves_rejected(L):
