@@ -305,10 +305,18 @@ bool inject_krylov_fault() {
 // stream before the host waits for column j (two result slots, a pinned
 // mirror each): the GPU never idles on the host.  When step j converges,
 // the queued step j + 1 is discarded.
+// The float multigrid hierarchy as the preconditioner of a double FGMRES
+// (the FP64 finish of the mixed path): the V-cycle runs in float on the float
+// linearisation (ut, dl), between conversions of v and z.
+struct Mg32 {
+  const float *ut = nullptr, *dl = nullptr;
+  float *vin = nullptr, *zout = nullptr;
+};
+
 template <typename T>
 chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, const T *Binv, bool coarse,
                    bool mg, const double *b, double *x, const chns_solver_opts &o, int *its_out, Timer &tj,
-                   cudaStream_t st) {
+                   cudaStream_t st, const Mg32 *mg32 = nullptr, bool *converged = nullptr) {
   Workspace &ws = m->ws;
   const int nf = m->nf;
   const int64_t n = m->n_nodes * nf;
@@ -353,7 +361,13 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     double *h1 = hd + 3 * K * sl, *h2 = h1 + K, *nr = h1 + 2 * K;
     T *vj = V + (int64_t)j * ld, *w = V + (int64_t)(j + 1) * ld;
     T *zj = Z + (int64_t)j * ld;
-    if (mg) TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
+    if (mg32) {
+      vec_convert<T, float>(vj, mg32->vin, n, 1.0, s);
+      TRY(mg_apply<float>(m, pc, mg32->ut, mg32->dl, mg32->vin, mg32->zout, s));
+      vec_convert<float, T>(mg32->zout, zj, n, 1.0, s);
+    } else if (mg) {
+      TRY(mg_apply<T>(m, pc, ut, dl, vj, zj, s));
+    }
     else precond_apply<T>(m, Binv, coarse, vj, zj, s);
     int ev = 0;
     if (cap) CHNS_CUDA_TRY(cudaEventRecordWithFlags(G.jv[2 * j], s, cudaEventRecordExternal));
@@ -383,7 +397,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     key.p[11] = m->coarse.Minv32.as<void>(); key.p[12] = m->coarse.cnodes; key.p[13] = Ebuf;
     key.p[14] = ctr; key.p[15] = mg ? m->mg : nullptr;
     key.i[0] = ld; key.i[1] = n; key.i[2] = coarse; key.i[3] = m->coarse.ready; key.i[4] = m->coarse.level;
-    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph;
+    key.i[5] = mg ? (int64_t)m->mg->generation : -1; key.i[6] = o.use_graph + 2 * (mg32 != nullptr);
     key.i[7] = m->jv_variant;
     key.pc = pc;
     const unsigned char *kb = reinterpret_cast<const unsigned char *>(&key);
@@ -440,6 +454,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
   };
   std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), yk(mr);
   int total = 0;
+  bool conv = false;
   while (true) {
     // V_0 = r / beta
     vec_convert<double, T>(r, V, n, 1.0 / beta, st);
@@ -497,6 +512,7 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     }
     CHNS_CUDA_TRY(cudaMemcpyAsync(cz, yk.data(), sizeof(double) * j_end, cudaMemcpyHostToDevice, st));
     vec_combine<T>(Z, ld, j_end, cz, x, n, st);
+    if (done) conv = true;
     if (done || total >= o.krylov_max_it) break;
     // restart: r = b - J x
     vec_convert<double, T>(x, tv, n, 1.0, st);
@@ -508,9 +524,10 @@ chns_status fgmres(chns_mesh *m, const PhysCoef &pc, const T *ut, const T *dl, c
     TRY(norm2(m, r, &beta, st));
     TRY(tj.collect());
     if (!std::isfinite(beta)) { set_error("non-finite Krylov residual"); return CHNS_ERR_NONFINITE; }
-    if (beta <= target) break;
+    if (beta <= target) { conv = true; break; }
   }
   *its_out = total;
+  if (converged) *converged = conv;
   TRY(tj.finish());
   return check_launch();
 }
@@ -726,13 +743,34 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
       } else {
         double *ut_t = nullptr, *dl_t = nullptr;
         TRY(prepare<double>(m, U, Un, st, &ut_t, &dl_t));
+        Mg32 mg32;
+        bool use_mg32 = false;
         if (mixed) {
-          if (use_mg) {
-            // the FP64 finish: V-cycles with operators and smoother blocks
-            // probed in double (the weakly determined modes it must resolve
-            // are where float probes fall short: on the 7M-leaf mesh float
-            // blocks, promoted, left FGMRES at its iteration cap); built once
-            // and kept next to the float ones until the next float build
+          if (use_mg && !m->mg->finish64) {
+            // the FP64 finish first keeps the float hierarchy as its
+            // preconditioner (FGMRES is flexible): float V-cycles, cheap
+            float *u32 = nullptr, *d32 = nullptr;
+            TRY(prepare<float>(m, U, Un, st, &u32, &d32));
+            if (!m->mg->ready[0]) {
+              TRY(mg_build<float>(m, pcs, u32, d32, o.mg_omega, o.mg_smooth, st));
+              tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+            } else {
+              TRY(mg_update_state<float>(m, u32, d32, st));
+            }
+            TRY(ws.p32a.ensure(sizeof(float) * n + 16));
+            TRY(ws.p32b.ensure(sizeof(float) * n + 16));
+            mg32.ut = u32;
+            mg32.dl = d32;
+            mg32.vin = ws.p32a.as<float>();
+            mg32.zout = ws.p32b.as<float>();
+            use_mg32 = true;
+          } else if (use_mg) {
+            // float V-cycles could not precondition the FP64 operator on this
+            // mesh (FGMRES missed its tolerance): V-cycles with operators and
+            // smoother blocks probed in double (the weakly determined modes
+            // the finish must resolve are where float probes fall short);
+            // built once and kept next to the float ones until the next float
+            // build
             if (!m->mg->ready[1]) {
               TRY(mg_build<double>(m, pcs, ut_t, dl_t, o.mg_omega, o.mg_smooth, st, true));
               tp.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
@@ -757,7 +795,19 @@ chns_status newton_step(chns_mesh *m, const chns_params *p, const chns_solver_op
         } else if (use_mg) {
           TRY(mg_update_state<double>(m, ut_t, dl_t, st));
         }
-        TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st));
+        if (use_mg32) {
+          // a bounded trial: if the float V-cycles cannot bring the FP64
+          // correction to its tolerance within two restart cycles, this mesh
+          // switches to double V-cycles for every later finish
+          chns_solver_opts ot = oi;
+          ot.krylov_max_it = std::min(o.krylov_max_it, 2 * o.krylov_restart);
+          bool conv = false;
+          TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, ot, &k, tk, st,
+                             &mg32, &conv));
+          if (!conv) m->mg->finish64 = true;
+        } else {
+          TRY(fgmres<double>(m, pcs, ut_t, dl_t, ws.binv64.as<double>(), coarse, use_mg, F, dU, oi, &k, tk, st));
+        }
         if (mixed) ++its64;
       }
       tj.ms += tk.ms;
@@ -961,7 +1011,7 @@ void chns_mesh_destroy(chns_mesh *m) {
   m->ws.F.release(); m->ws.dU.release(); m->ws.r.release(); m->ws.V.release(); m->ws.Z.release();
   m->ws.wv.release(); m->ws.yv.release(); m->ws.binv.release(); m->ws.binv64.release(); m->ws.red.release(); m->ws.hdev.release();
   m->ws.e32.release(); m->ws.e64.release(); m->ws.ctr.release(); m->ws.count.release();
-  m->ws.Ublk.release();
+  m->ws.Ublk.release(); m->ws.p32a.release(); m->ws.p32b.release();
   delete m;
   cudaSetDevice(prev);
 }

@@ -60,6 +60,7 @@ struct Workspace {
   DevBuf ut, dl, ut32, dl32, f;        // prepared nodal fields (time averages / increments)
   DevBuf F, dU, r;                     // double n_dof
   DevBuf Ublk;                         // double n_dof: the previous block-iteration state
+  DevBuf p32a, p32b;                   // float n_dof: float V-cycle input / output in the FP64 finish
   DevBuf V;                            // double (m+1) n_dof Krylov basis
   DevBuf Z;                            // (m) n_dof preconditioned directions (float or double)
   DevBuf wv, yv;                       // float/double n_dof work vectors

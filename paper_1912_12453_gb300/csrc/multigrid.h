@@ -32,6 +32,7 @@ struct Multigrid {
   int smooth = 1;
   uint64_t generation = 0;                   // bumped at every build (graph keys)
   bool autotune = false;                     // tune the J.w schedule of every level
+  bool finish64 = false;                     // the FP64 finish needs double V-cycles on this mesh
 };
 
 // hierarchy of coarsened meshes and transfers down to a uniform level `bottom`
