@@ -283,7 +283,7 @@ def field_diffs(a, b, nf, dim):
     return out
 
 
-def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier):
+def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier, legs=("fp32_mixed", "fp64")):
     """FP32-bulk mixed vs plain FP64 CN steps from the same state, both to the
     same Newton tolerance: seconds per step (CUDA events), iteration counts,
     per-field solution differences."""
@@ -291,6 +291,8 @@ def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier):
     out = {}
     finals = {}
     for name, opts in (("fp32_mixed", opts32), ("fp64", opts64)):
+        if name not in legs:
+            continue
         Ua, Ub = U0.clone(), torch.empty_like(U0)
         try:
             chns.step(mesh, wl.params, Ua, Ub, opts)  # warm-up (builds graphs and the preconditioner)
@@ -435,6 +437,7 @@ def main():
                     help="comma-separated further workloads for the FP32-vs-FP64 step comparison "
                          "(bubble3d_l5_9, merge3d_l6_10, batchedN = N batched instances; empty: none)")
     ap.add_argument("--extra-steps", type=int, default=2)
+    ap.add_argument("--extra-legs", default="fp32,fp64", help="precisions timed on the extra workloads")
     ap.add_argument("--preconditioner", default="multigrid", choices=["multigrid", "two_level"])
     ap.add_argument("--mg-omega", type=float, default=0.4)
     ap.add_argument("--mg-smooth", type=int, default=1)
@@ -646,7 +649,8 @@ def main():
             Ux = torch.from_numpy(W.initial_state(mx.coords, wx).reshape(-1)).to(dev)
             chns.init_mu(mx, wx.params, Ux)
             log(f"{name}: {mx.n_elem} leaves, {mx.n_dof} DoF, {mx.n_hanging} hanging nodes")
-            r = compare_steps(chns, wx, mx, Ux, args.extra_steps, opts32, opts64, dev, barrier)
+            legs = tuple({"fp32": "fp32_mixed", "fp64": "fp64"}[x] for x in args.extra_legs.split(","))
+            r = compare_steps(chns, wx, mx, Ux, args.extra_steps, opts32, opts64, dev, barrier, legs)
             r.update({"workload": DESCRIPTION.get(name, name), "leaves": mx.n_elem, "n_dof": mx.n_dof,
                       "hanging_nodes": mx.n_hanging, "newton_rtol": args.newton_rtol})
             extra[name] = r

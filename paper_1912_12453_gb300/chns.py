@@ -23,10 +23,10 @@ CHNS_PC_MULTIGRID = 1
 JACVEC_VARIANTS = ["element-local buffer + node gather, 128-thread blocks, 6/SM",
                    "element-local buffer + node gather, 256-thread blocks, 3/SM",
                    "element-local buffer + node gather, 64-thread blocks, 12/SM",
-                   "element-local buffer + node gather, 128-thread blocks, 8/SM (64 registers)",
+                   "element-local buffer + node gather, 128-thread blocks, 8/SM (at most 64 registers)",
                    "element colours, in-place adds into y, 128-thread blocks",
-                   "element-local buffer + node gather, 128-thread blocks, 5/SM (102 registers)",
-                   "element-local buffer + node gather, 128-thread blocks, 4/SM (128 registers)"]
+                   "element-local buffer + node gather, 128-thread blocks, 5/SM (at most 102 registers)",
+                   "element-local buffer + node gather, 128-thread blocks, 4/SM (at most 128 registers)"]
 STATUS = {0: "CHNS_OK", 1: "CHNS_ERR_ARG", 2: "CHNS_ERR_MESH", 3: "CHNS_ERR_CUDA",
           4: "CHNS_ERR_NONFINITE", 5: "CHNS_ERR_NEWTON", 6: "CHNS_ERR_KRYLOV",
           8: "CHNS_ERR_OOM"}
