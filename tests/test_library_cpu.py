@@ -123,3 +123,44 @@ def test_generated_octrees_are_balanced_and_sorted():
         assert np.all(np.diff(keys.astype(np.int64)) > 0)
         vol = np.sum(1.0 / (1 << (L_.dim * L_.level.astype(np.int64))))
         assert abs(vol - 1.0) < 1e-12
+
+
+def test_batched_workload_generator():
+    """64 independent instances from one seed: both dimensions, levels 6-9 in
+    2D and 5-7 in 3D, parameters in the stated ranges, every octree sorted,
+    tiling the box and 2:1 balanced (checked by its own neighbour search)."""
+    wls = W.batched_workloads(64)
+    assert len(wls) == 64
+    dims = [w.params.dim for w in wls]
+    assert 0 < dims.count(2) < 64
+    for w in wls:
+        L = w.leaves
+        top = int(L.level.max())
+        assert (6 <= top <= 9) if L.dim == 2 else (5 <= top <= 7)
+        assert 1e-3 <= w.params.rho_ratio <= 1.0 and 1e-2 <= w.params.eta_ratio <= 1.0
+        assert 0.1 <= w.spheres[0].radius <= 0.25
+        keys = W.morton_keys(L.anchor, L.max_level).astype(np.int64)
+        assert np.all(np.diff(keys) > 0)
+        vol = np.sum(1.0 / (1 << (L.dim * L.level.astype(np.int64))))
+        assert abs(vol - 1.0) < 1e-12
+    # 2:1 balance of the six smallest instances by brute force: the level of
+    # every max-level cell next to a leaf's corners differs from the leaf's by
+    # at most one
+    import itertools
+    for w in sorted(wls, key=lambda w: w.leaves.n)[:6]:
+        L = w.leaves
+        size = 1 << L.max_level
+        lev = L.level.astype(np.int64)
+        anc = L.anchor.astype(np.int64)
+        lookup = {}
+        for a, l in zip(anc, lev):
+            s = 1 << (L.max_level - l)
+            for off in itertools.product(range(s), repeat=L.dim):
+                lookup[tuple(a + np.array(off))] = l
+        assert len(lookup) == size ** L.dim
+        for a, l in zip(anc, lev):
+            s = 1 << (L.max_level - l)
+            for off in itertools.product((-1, 0, s), repeat=L.dim):
+                q = tuple(a + np.array(off))
+                if all(0 <= x < size for x in q):
+                    assert abs(lookup[q] - l) <= 1

@@ -509,3 +509,19 @@ def test_mms_temporal_rate_phi_2d():
     d = [np.linalg.norm(phis[i] - phis[i + 1]) for i in range(3)]
     rates = [math.log2(d[i] / d[i + 1]) for i in range(2)]
     assert all(r > 1.7 for r in rates), rates
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_threaded_jacvec_equals_the_serial_one(dim):
+    """The all-core CPU baseline runs the same element routine grouped by the
+    oracle's own colouring: its J.w must equal the serial one to rounding (the
+    contributions to a row arrive in colour order instead of element order)."""
+    L = W.band_leaves(dim, 2, 4 if dim == 3 else 6, [W.Sphere((0.5, 0.45, 0.4)[:dim], 0.25)], 0.04)
+    m = O.OracleMesh(L)
+    rng = np.random.default_rng(3)
+    prm = _params(dim)
+    Un, Uo, w = (rng.uniform(-1, 1, m.n_dof) for _ in range(3))
+    y1 = m.jacvec(prm, Un, Uo, w)
+    for threads in (1, 3, 8):
+        yt = m.jacvec_threads(prm, Un, Uo, w, threads)
+        assert np.linalg.norm(yt - y1) <= 1e-14 * np.linalg.norm(y1)
