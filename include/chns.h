@@ -303,6 +303,81 @@ chns_status chns_batch_step(chns_batch *batch, const chns_solver_opts *opts,
 
 void chns_batch_destroy(chns_batch *batch);
 
+/* ---------------------------------------------------------- remeshing (host)
+ *
+ * Sec. 4: every few time steps the octree is re-refined around the current
+ * interface, 2:1 balanced, meshed again, and the fields are carried from the
+ * old mesh to the new one by interpolation ("Refinement", "2:1 Balancing",
+ * "Intergrid transfers").  These calls work on HOST arrays only and need no
+ * GPU.  Leaf lists follow chns_mesh_create: level[n] and anchor[n*dim] (x
+ * fastest, max_level resolution), in Morton order, tiling the box; a leaf
+ * list passed in must satisfy that (otherwise CHNS_ERR_MESH), but need not be
+ * balanced.  Nodal fields are host arrays U[n_nodes*nf] over the independent
+ * nodes of the leaf list's mesh, whose integer coordinates are
+ * xyz[n_nodes*dim] (chns_mesh_node_coords); hanging nodes take the mean of
+ * the corners of the coarser edge or face they lie on.  Leaf lists that a
+ * call returns are allocated by the library: release each array with
+ * chns_leaves_free. */
+
+/* The leaves a mesh was built from (host outputs level[n_leaves],
+ * anchor[n_leaves*dim], Morton order).  CHNS_ERR_ARG for a batch's union
+ * mesh. */
+chns_status chns_mesh_leaves(const chns_mesh *mesh, uint8_t *level, uint32_t *anchor);
+
+/* One adaptation pass: mark[e] = +1 splits leaf e into its 2^dim children
+ * (ignored at max_level), -1 merges a family into its parent when all 2^dim
+ * children are leaves marked -1 (ignored at level 0), 0 keeps it (mark NULL:
+ * all 0).  Then the tree is 2:1 balanced across faces, edges and corners by
+ * splitting leaves only (a merge that would break the balance is undone): the
+ * result is the coarsest balanced refinement of the marked tree.  Outputs
+ * *n_out, *level_out, *anchor_out (library-allocated, Morton order). */
+chns_status chns_leaves_adapt(int dim, int max_level, int64_t n, const uint8_t *level,
+                              const uint32_t *anchor, const int8_t *mark, int64_t *n_out,
+                              uint8_t **level_out, uint32_t **anchor_out);
+
+/* Intergrid transfer: the values at n_points integer points
+ * (points[n_points*dim], each in [0, 2^max_level]^dim) of the nodal Q1 field
+ * U on the leaf list (level, anchor): multilinear interpolation in the leaf
+ * whose cell holds the point, hanging corners interpolated.  Evaluated at
+ * the nodes of a refined or coarsened mesh this is the parent-to-child
+ * interpolation (refinement) and injection (coarsening) of the paper's
+ * transfer.  Host output out[n_points*nf].  A point outside the box is
+ * CHNS_ERR_ARG; a leaf corner that is neither a node in xyz nor a hanging
+ * node is CHNS_ERR_MESH. */
+chns_status chns_leaves_transfer(int dim, int max_level, int64_t n_leaves, const uint8_t *level,
+                                 const uint32_t *anchor, int64_t n_nodes, const int64_t *xyz,
+                                 int nf, const double *U, int64_t n_points, const int64_t *points,
+                                 double *out);
+
+/* Interface marks of the leaf list (level, anchor) against component
+ * phi_index of the field U on the source leaf list (src_level, src_anchor):
+ * a leaf meets the interface when the field's phi, interpolated at one of its
+ * corners, has |phi| <= band, or its corners carry both signs of phi (the
+ * corner test of Sec. 4 "Refinement" applied to the diffuse interface).  Its
+ * target level is level_max if it meets the interface, level_min otherwise;
+ * mark[e] = +1 below the target, -1 above it, 0 at it (host output mark[n]).
+ * A non-finite phi is CHNS_ERR_NONFINITE. */
+chns_status chns_leaves_mark_interface(int dim, int max_level, int64_t n_src,
+                                       const uint8_t *src_level, const uint32_t *src_anchor,
+                                       int64_t n_nodes, const int64_t *xyz, int nf, const double *U,
+                                       int phi_index, double band, int level_min, int level_max,
+                                       int64_t n, const uint8_t *level, const uint32_t *anchor,
+                                       int8_t *mark);
+
+/* Remesh around the interface of U's phi component: starting from the
+ * source leaf list, alternate chns_leaves_mark_interface (always against the
+ * source field) and chns_leaves_adapt until no leaf is marked or a pass
+ * changes nothing (at most 2 max_level + 2 passes; *passes, nullable, gets
+ * the count).  Outputs as chns_leaves_adapt. */
+chns_status chns_leaves_remesh(int dim, int max_level, int64_t n_src, const uint8_t *src_level,
+                               const uint32_t *src_anchor, int64_t n_nodes, const int64_t *xyz,
+                               int nf, const double *U, int phi_index, double band, int level_min,
+                               int level_max, int64_t *n_out, uint8_t **level_out,
+                               uint32_t **anchor_out, int *passes);
+
+/* Releases an array returned by chns_leaves_adapt or chns_leaves_remesh. */
+void chns_leaves_free(void *p);
+
 const char *chns_last_error(void);
 
 /* Tracing: number of kernels this library has launched in this process so

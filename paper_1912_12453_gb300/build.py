@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchns.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["mesh.cpp", "element.cu", "vector.cu", "coarse.cu", "api.cu", "noalloc.cu", "multigrid.cu", "peak.cu"]
+SOURCES = ["mesh.cpp", "octree.cpp", "element.cu", "vector.cu", "coarse.cu", "api.cu", "noalloc.cu", "multigrid.cu", "peak.cu"]
 # the FMA-peak measurement of the benchmark's roofline: a library of its own
 PEAK_SOURCES = ["peak.cu"]
 PEAK_OUT = os.path.join(HERE, "libchns_peak.so")

@@ -35,7 +35,8 @@ EXPORTS = ["chns_mesh_create", "chns_mesh_info", "chns_mesh_node_coords", "chns_
            "chns_residual", "chns_jacvec", "chns_init_mu", "chns_step", "chns_energy_mass",
            "chns_batch_create", "chns_batch_step", "chns_batch_destroy", "chns_last_error",
            "chns_kernel_launches", "chns_energy_mass_noalloc", "chns_tau_floor_count",
-           "chns_mesh_check", "chns_mesh_jacvec_schedule"]
+           "chns_mesh_check", "chns_mesh_jacvec_schedule", "chns_mesh_leaves", "chns_leaves_adapt",
+           "chns_leaves_transfer", "chns_leaves_mark_interface", "chns_leaves_remesh", "chns_leaves_free"]
 
 
 class ChnsError(RuntimeError):
@@ -139,6 +140,20 @@ def lib():
         L.chns_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.chns_batch_destroy.argtypes = [vp]
         L.chns_batch_destroy.restype = None
+        L.chns_mesh_leaves.restype = st
+        L.chns_mesh_leaves.argtypes = [vp, vp, vp]
+        L.chns_leaves_adapt.restype = st
+        L.chns_leaves_adapt.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp]
+        L.chns_leaves_transfer.restype = st
+        L.chns_leaves_transfer.argtypes = [i32, i32, i64, vp, vp, i64, vp, i32, vp, i64, vp, vp]
+        L.chns_leaves_mark_interface.restype = st
+        L.chns_leaves_mark_interface.argtypes = [i32, i32, i64, vp, vp, i64, vp, i32, vp, i32,
+                                                 ctypes.c_double, i32, i32, i64, vp, vp, vp]
+        L.chns_leaves_remesh.restype = st
+        L.chns_leaves_remesh.argtypes = [i32, i32, i64, vp, vp, i64, vp, i32, vp, i32, ctypes.c_double,
+                                         i32, i32, vp, vp, vp, vp]
+        L.chns_leaves_free.restype = None
+        L.chns_leaves_free.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -187,7 +202,15 @@ class Mesh:
         _check(L.chns_mesh_node_coords(h, self.coords_int.ctypes.data))
         lo_a = np.asarray(lo[: self.dim], dtype=np.float64)
         hi_a = np.asarray(hi[: self.dim], dtype=np.float64)
+        self.lo, self.hi = tuple(lo), tuple(hi)
         self.coords = lo_a + self.coords_int * ((hi_a - lo_a) / float(1 << self.max_level))
+
+    def leaves(self) -> "Leaves":
+        """The leaves the mesh was built from (Morton order)."""
+        lev = np.zeros(self.n_elem, dtype=np.uint8)
+        anc = np.zeros((self.n_elem, self.dim), dtype=np.uint32)
+        _check(lib().chns_mesh_leaves(self._h, lev.ctypes.data, anc.ctypes.data))
+        return Leaves(self.dim, self.max_level, lev, anc)
 
     @property
     def handle(self):
@@ -214,6 +237,117 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+class Leaves:
+    """A leaf list: level[n] (uint8) and anchor[n, dim] (uint32), Morton order."""
+
+    def __init__(self, dim: int, max_level: int, level, anchor):
+        self.dim, self.max_level = int(dim), int(max_level)
+        self.level = np.ascontiguousarray(level, dtype=np.uint8)
+        self.anchor = np.ascontiguousarray(np.asarray(anchor, dtype=np.uint32).reshape(-1, self.dim))
+
+    @property
+    def n(self) -> int:
+        return int(self.level.shape[0])
+
+
+def _leaf_arrays(leaves):
+    lev = np.ascontiguousarray(leaves.level, dtype=np.uint8)
+    anc = np.ascontiguousarray(leaves.anchor, dtype=np.uint32)
+    return lev, anc
+
+
+def _take_leaves(dim, max_level, n, lp, ap) -> Leaves:
+    try:
+        m = n.value
+        lev = np.ctypeslib.as_array(ctypes.cast(lp, ctypes.POINTER(ctypes.c_uint8)), shape=(m,)).copy()
+        anc = np.ctypeslib.as_array(ctypes.cast(ap, ctypes.POINTER(ctypes.c_uint32)), shape=(m * dim,)).copy()
+    finally:
+        lib().chns_leaves_free(lp)
+        lib().chns_leaves_free(ap)
+    return Leaves(dim, max_level, lev, anc)
+
+
+def _field(U, xyz, nf):
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+    xyz = np.ascontiguousarray(xyz, dtype=np.int64)
+    if U.shape[0] != xyz.shape[0] * nf:
+        raise ValueError("field size does not match the node count")
+    return U, xyz
+
+
+def leaves_adapt(leaves, mark=None) -> Leaves:
+    """One split / merge pass by marks (+1, -1, 0), then 2:1 balance (host)."""
+    lev, anc = _leaf_arrays(leaves)
+    mk = None if mark is None else np.ascontiguousarray(mark, dtype=np.int8)
+    if mk is not None and mk.shape[0] != lev.shape[0]:
+        raise ValueError("one mark per leaf")
+    n, lp, ap = ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().chns_leaves_adapt(leaves.dim, leaves.max_level, lev.shape[0], lev.ctypes.data, anc.ctypes.data,
+                                   None if mk is None else mk.ctypes.data, ctypes.byref(n), ctypes.byref(lp),
+                                   ctypes.byref(ap)))
+    return _take_leaves(leaves.dim, leaves.max_level, n, lp, ap)
+
+
+def leaves_transfer(leaves, xyz, U, points, nf: Optional[int] = None) -> np.ndarray:
+    """Values at integer points of the nodal Q1 field U (host, [n_nodes, nf])."""
+    nf = int(nf if nf is not None else leaves.dim + 3)
+    lev, anc = _leaf_arrays(leaves)
+    U, xyz = _field(U, xyz, nf)
+    pts = np.ascontiguousarray(points, dtype=np.int64)
+    out = np.zeros((pts.shape[0], nf), dtype=np.float64)
+    _check(lib().chns_leaves_transfer(leaves.dim, leaves.max_level, lev.shape[0], lev.ctypes.data,
+                                      anc.ctypes.data, xyz.shape[0], xyz.ctypes.data, nf, U.ctypes.data,
+                                      pts.shape[0], pts.ctypes.data, out.ctypes.data))
+    return out
+
+
+def leaves_mark_interface(src, xyz, U, leaves, level_min: int, level_max: int, phi_band: float = 0.9,
+                          nf: Optional[int] = None, phi_index: Optional[int] = None) -> np.ndarray:
+    """Interface marks (+1, -1, 0) of a leaf list against the phi of U on src (host)."""
+    nf = int(nf if nf is not None else src.dim + 3)
+    phi_index = int(phi_index if phi_index is not None else src.dim + 1)
+    slev, sanc = _leaf_arrays(src)
+    lev, anc = _leaf_arrays(leaves)
+    U, xyz = _field(U, xyz, nf)
+    mark = np.zeros(lev.shape[0], dtype=np.int8)
+    _check(lib().chns_leaves_mark_interface(src.dim, src.max_level, slev.shape[0], slev.ctypes.data,
+                                            sanc.ctypes.data, xyz.shape[0], xyz.ctypes.data, nf, U.ctypes.data,
+                                            phi_index, float(phi_band), int(level_min), int(level_max),
+                                            lev.shape[0], lev.ctypes.data, anc.ctypes.data, mark.ctypes.data))
+    return mark
+
+
+def leaves_remesh(src, xyz, U, level_min: int, level_max: int, phi_band: float = 0.9,
+                  nf: Optional[int] = None, phi_index: Optional[int] = None):
+    """Leaves refined to level_max around the interface of U's phi and
+    coarsened to level_min elsewhere, 2:1 balanced (host).  Returns
+    (Leaves, passes)."""
+    nf = int(nf if nf is not None else src.dim + 3)
+    phi_index = int(phi_index if phi_index is not None else src.dim + 1)
+    slev, sanc = _leaf_arrays(src)
+    U, xyz = _field(U, xyz, nf)
+    n, lp, ap, passes = ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()
+    _check(lib().chns_leaves_remesh(src.dim, src.max_level, slev.shape[0], slev.ctypes.data, sanc.ctypes.data,
+                                    xyz.shape[0], xyz.ctypes.data, nf, U.ctypes.data, phi_index,
+                                    float(phi_band), int(level_min), int(level_max), ctypes.byref(n),
+                                    ctypes.byref(lp), ctypes.byref(ap), ctypes.byref(passes)))
+    return _take_leaves(src.dim, src.max_level, n, lp, ap), passes.value
+
+
+def remesh(mesh: Mesh, U, level_min: int, level_max: int, phi_band: float = 0.9):
+    """Remesh around the interface of the device state U and transfer U:
+    returns (new Mesh, new device state, passes).  The octree work and the
+    interpolation run in the library on the host; U is copied to the host and
+    the transferred state back to U's device."""
+    import torch
+    src = mesh.leaves()
+    U_host = U.detach().to("cpu", torch.float64).numpy()
+    new_leaves, passes = leaves_remesh(src, mesh.coords_int, U_host, level_min, level_max, phi_band, mesh.nf)
+    new_mesh = Mesh(new_leaves, mesh.lo, mesh.hi)
+    U_new = leaves_transfer(src, mesh.coords_int, U_host, new_mesh.coords_int, mesh.nf)
+    return new_mesh, torch.from_numpy(U_new.reshape(-1)).to(U.device), passes
 
 
 def residual(mesh: Mesh, params, U_new, U_old, forcing=None, bc=None, out=None, stream=None):

@@ -149,6 +149,8 @@ struct chns_mesh {
   std::vector<const chns_mesh *> inst_meshes;  // union: the instance meshes (not owned)
   int64_t n_wall = 0;
   std::vector<int64_t> node_xyz;       // host: n_nodes * dim integer coordinates
+  std::vector<uint8_t> leaf_level;     // host: the leaves as given (Morton order), plain meshes
+  std::vector<uint32_t> leaf_anchor;   // host: n_elem * dim
   // device arrays
   int32_t *conn = nullptr;             // n_elem * nc: node index, or -(h+1) for hanging corner h
   uint8_t *level = nullptr;            // n_elem

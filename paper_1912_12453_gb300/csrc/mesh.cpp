@@ -394,6 +394,8 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
   m->n_hang = n_hang;
   m->n_wall = (int64_t)wall.size();
   m->node_xyz = std::move(node_xyz);
+  m->leaf_level.assign(level, level + n);
+  m->leaf_anchor.assign(anchor, anchor + n * dim);
 
   chns_status st;
   CHNS_CUDA_TRY(cudaGetDevice(&m->device));
