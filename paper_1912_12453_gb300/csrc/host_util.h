@@ -13,41 +13,59 @@
 
 namespace chns {
 
-// Open-addressing hash map from a 64-bit key to a 32-bit value.
+// Open-addressing hash map from a 64-bit key to a 64-bit value (linear
+// probing; key and value side by side, one cache line per probe).
 class KeyMap {
  public:
   explicit KeyMap(size_t expected) {
     size_t cap = 16;
     while (cap < expected * 2) cap <<= 1;
-    keys_.assign(cap, kEmpty);
-    vals_.assign(cap, 0);
+    slots_.assign(cap, Slot{kEmpty, 0});
     mask_ = cap - 1;
   }
-  // returns (value, inserted)
+  // returns (value, inserted); the table doubles when it is half full
   std::pair<int64_t, bool> insert(uint64_t key, int64_t value) {
+    if (2 * (size_ + 1) > slots_.size()) grow();
     size_t i = hash(key) & mask_;
     while (true) {
-      if (keys_[i] == kEmpty) {
-        keys_[i] = key;
-        vals_[i] = value;
+      Slot &sl = slots_[i];
+      if (sl.key == kEmpty) {
+        sl.key = key;
+        sl.val = value;
         ++size_;
         return {value, true};
       }
-      if (keys_[i] == key) return {vals_[i], false};
+      if (sl.key == key) return {sl.val, false};
       i = (i + 1) & mask_;
     }
   }
   int64_t find(uint64_t key) const {
     size_t i = hash(key) & mask_;
     while (true) {
-      if (keys_[i] == kEmpty) return -1;
-      if (keys_[i] == key) return vals_[i];
+      const Slot &sl = slots_[i];
+      if (sl.key == kEmpty) return -1;
+      if (sl.key == key) return sl.val;
       i = (i + 1) & mask_;
     }
   }
   size_t size() const { return size_; }
 
  private:
+  struct Slot {
+    uint64_t key;
+    int64_t val;
+  };
+  void grow() {
+    std::vector<Slot> old = std::move(slots_);
+    slots_.assign(old.size() * 2, Slot{kEmpty, 0});
+    mask_ = slots_.size() - 1;
+    for (const Slot &o : old) {
+      if (o.key == kEmpty) continue;
+      size_t i = hash(o.key) & mask_;
+      while (slots_[i].key != kEmpty) i = (i + 1) & mask_;
+      slots_[i] = o;
+    }
+  }
   static constexpr uint64_t kEmpty = ~uint64_t(0);
   static uint64_t hash(uint64_t x) {
     x += 0x9e3779b97f4a7c15ull;
@@ -55,8 +73,7 @@ class KeyMap {
     x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
     return x ^ (x >> 31);
   }
-  std::vector<uint64_t> keys_;
-  std::vector<int64_t> vals_;
+  std::vector<Slot> slots_;
   size_t mask_ = 0, size_ = 0;
 };
 
@@ -75,11 +92,30 @@ inline uint64_t okey(int level, const int64_t *x, int dim, int max_level) {
   return pack(c, dim);
 }
 
-inline uint64_t morton(const uint32_t *a, int dim, int max_level) {
-  uint64_t k = 0;
-  for (int b = 0; b <= max_level; ++b)
-    for (int ax = 0; ax < dim; ++ax) k |= uint64_t((a[ax] >> b) & 1u) << (dim * b + ax);
-  return k;
+// Morton key: bit b of coordinate ax goes to bit dim*b + ax.  Coordinates
+// are at most 2^20 (max_level <= 20), so bits 0..20 of each are spread: every
+// bit moves to a multiple of dim by shift-and-mask steps of halving width.
+inline uint64_t spread2(uint64_t x) {  // bits 0..31 -> even bits
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+inline uint64_t spread3(uint64_t x) {  // bits 0..20 -> every third bit
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+inline uint64_t morton(const uint32_t *a, int dim, int /*max_level*/) {
+  if (dim == 2) return spread2(a[0]) | (spread2(a[1]) << 1);
+  return spread3(a[0]) | (spread3(a[1]) << 1) | (spread3(a[2]) << 2);
 }
 
 template <class T>
