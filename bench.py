@@ -326,6 +326,66 @@ def compare_steps(chns, wl, mesh, U0, steps, opts32, opts64, dev, barrier, legs=
     return out
 
 
+def remesh_leg(chns, wl, mesh, U, steps, opts32, dev, barrier, shift_cells=4):
+    """Remesh around the interface of a state (Sec. 4 "Intergrid transfers":
+    marks from the corner test on phi, adaptation passes with 2:1 balance, a
+    new mesh, the Q1 transfer of the state), project mu on the new mesh, then
+    CN steps there, the first one included (it builds the preconditioner and
+    tunes the J.w schedule): the paper's own measurement is the time for 5
+    steps including remeshing.  The state is U with phi replaced by the
+    profile of the spheres moved by shift_cells finest cells along the last
+    axis (a stand-in for several steps of rise, so that the remesh refines and
+    coarsens).  Host stages timed by the wall clock, the steps by CUDA events."""
+    import torch
+    level_min, level_max = int(wl.leaves.level.min()), int(wl.leaves.level.max())
+    dim = mesh.dim
+    h = shift_cells / float(1 << wl.leaves.max_level)
+    moved = [W.Sphere(tuple(c + (h if k == dim - 1 else 0.0) for k, c in enumerate(sp.center)), sp.radius)
+             for sp in wl.spheres]
+    Um = U.detach().clone().view(-1, mesh.nf)
+    Um[:, dim + 1] = torch.from_numpy(W.phi_profile(mesh.coords, moved, wl.params.Cn, wl.bubble)).to(dev)
+    barrier()
+    t0 = time.perf_counter()
+    src = mesh.leaves()
+    U_host = Um.to("cpu", torch.float64).numpy()
+    t1 = time.perf_counter()
+    new_leaves, passes = chns.leaves_remesh(src, mesh.coords_int, U_host, level_min, level_max, 0.9, mesh.nf)
+    t2 = time.perf_counter()
+    nm = chns.Mesh(new_leaves, mesh.lo, mesh.hi)
+    t3 = time.perf_counter()
+    Un = torch.from_numpy(chns.leaves_transfer(src, mesh.coords_int, U_host, nm.coords_int, mesh.nf)
+                          .reshape(-1)).to(dev)
+    barrier()
+    t4 = time.perf_counter()
+    chns.init_mu(nm, wl.params, Un)
+    barrier()
+    t5 = time.perf_counter()
+    Ub = torch.empty_like(Un)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record()
+    for _ in range(steps):
+        stats.append(chns.step(nm, wl.params, Un, Ub, opts32))
+        Un, Ub = Ub, Un
+    e1.record()
+    barrier()
+    steps_s = e0.elapsed_time(e1) / 1e3
+    out = {"level_min": level_min, "level_max": level_max, "phi_band": 0.9, "passes": passes,
+           "leaves_before": mesh.n_elem, "leaves_after": nm.n_elem, "n_dof_after": nm.n_dof,
+           "host_threads": os.cpu_count(),
+           "state": f"phi of the spheres moved by {shift_cells} finest cells along the last axis",
+           "seconds": {"download": t1 - t0, "marks_adapt_balance": t2 - t1, "mesh_create": t3 - t2,
+                       "transfer_upload": t4 - t3, "remesh_total": t4 - t0, "mu_projection": t5 - t4},
+           "steps_after": steps, "steps_after_s": steps_s,
+           "newton_its": [s_["newton_its"] for s_ in stats],
+           "krylov_its": [s_["krylov_its_total"] for s_ in stats],
+           f"{steps}_steps_including_remesh_s": (t5 - t0) + steps_s}
+    log(wl.name, "remesh", f"{t4 - t0:.2f} s", f"{passes} passes", f"{mesh.n_elem} -> {nm.n_elem} leaves,",
+        f"mu {t5 - t4:.2f} s, {steps} steps {steps_s:.2f} s")
+    nm.close()
+    return out
+
+
 def compare_batch_steps(chns, n, steps, opts32, opts64, dev, barrier):
     """The batched workload: n independent droplet / bubble instances of
     uneven size and parameters (2D quadtrees to levels 6-9, 3D octrees to
@@ -438,6 +498,9 @@ def main():
                          "(bubble3d_l5_9, merge3d_l6_10, batchedN = N batched instances; empty: none)")
     ap.add_argument("--extra-steps", type=int, default=2)
     ap.add_argument("--extra-legs", default="fp32,fp64", help="precisions timed on the extra workloads")
+    ap.add_argument("--remesh-steps", type=int, default=5,
+                    help="after the steps of an adaptive extra workload: remesh its state, then this many FP32 "
+                         "CN steps on the new mesh (0: no remesh)")
     ap.add_argument("--preconditioner", default="multigrid", choices=["multigrid", "two_level"])
     ap.add_argument("--mg-omega", type=float, default=0.4)
     ap.add_argument("--mg-smooth", type=int, default=1)
@@ -653,6 +716,12 @@ def main():
             r = compare_steps(chns, wx, mx, Ux, args.extra_steps, opts32, opts64, dev, barrier, legs)
             r.update({"workload": DESCRIPTION.get(name, name), "leaves": mx.n_elem, "n_dof": mx.n_dof,
                       "hanging_nodes": mx.n_hanging, "newton_rtol": args.newton_rtol})
+            if args.remesh_steps > 0 and len(set(wx.leaves.level.tolist())) > 1:
+                try:
+                    r["remesh"] = remesh_leg(chns, wx, mx, Ux, args.remesh_steps, opts32, dev, barrier)
+                except Exception as ex:
+                    r["remesh"] = {"error": f"{type(ex).__name__}: {ex}"}
+                    log(name, "remesh failed:", ex)
             extra[name] = r
             mx.close()
             del Ux
