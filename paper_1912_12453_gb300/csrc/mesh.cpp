@@ -143,30 +143,36 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
         if (!oct.insert(okey(l, x, dim, max_level), 1).second) break;
       }
     }
-    int nnb = dim == 2 ? 9 : 27;
+    // the parents of the 3^dim - 1 neighbour cells: per axis the cells at
+    // a - s, a, a + s inside the box have at most two distinct parents, so
+    // at most 2^dim parents to look up (the leaf's own is always present)
     for (int64_t e = 0; e < n; ++e) {
       int l = level[e];
       if (l <= 1) continue;
       int64_t s = int64_t(1) << (max_level - l);
       int64_t ps = s * 2;
-      for (int q = 0; q < nnb; ++q) {
-        int64_t x[3];
-        int t = q;
-        bool self = true, inside = true;
-        for (int a = 0; a < dim; ++a) {
-          int o = t % 3 - 1;
-          t /= 3;
-          if (o) self = false;
-          x[a] = int64_t(anchor[e * dim + a]) + o * s;
-          if (x[a] < 0 || x[a] >= top) inside = false;
+      int64_t cand[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+      int nc3[3] = {1, 1, 1};
+      for (int a = 0; a < dim; ++a) {
+        const int64_t x0 = anchor[e * dim + a];
+        int cnt = 0;
+        for (int o = -1; o <= 1; ++o) {
+          const int64_t x = x0 + o * s;
+          if (x < 0 || x >= top) continue;
+          const int64_t p = (x / ps) * ps;
+          if (cnt == 0 || cand[a][cnt - 1] != p) cand[a][cnt++] = p;
         }
-        if (self || !inside) continue;
-        for (int a = 0; a < dim; ++a) x[a] = (x[a] / ps) * ps;
-        if (oct.find(okey(l - 1, x, dim, max_level)) < 0) {
-          set_error("mesh is not 2:1 balanced at leaf %lld", (long long)e);
-          return CHNS_ERR_MESH;
-        }
+        nc3[a] = cnt;
       }
+      for (int i0 = 0; i0 < nc3[0]; ++i0)
+        for (int i1 = 0; i1 < nc3[1]; ++i1)
+          for (int i2 = 0; i2 < nc3[2]; ++i2) {
+            int64_t x[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
+            if (oct.find(okey(l - 1, x, dim, max_level)) < 0) {
+              set_error("mesh is not 2:1 balanced at leaf %lld", (long long)e);
+              return CHNS_ERR_MESH;
+            }
+          }
     }
   }
 
@@ -280,6 +286,25 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     return int(std::unique(out, out + k) - out);
   };
 
+  // footprints of all elements (CSR) and the node -> elements incidence over
+  // them, in increasing element order (non-uniform meshes only)
+  std::vector<int64_t> fp_start, inc_start;
+  std::vector<int32_t> fp_node, inc_elem;
+  if (!uniform) {
+    std::vector<int32_t> fp(32);
+    fp_start.assign(size_t(n) + 1, 0);
+    for (int64_t e = 0; e < n; ++e) fp_start[e + 1] = fp_start[e] + footprint(e, fp.data());
+    fp_node.resize(size_t(fp_start[n]));
+    for (int64_t e = 0; e < n; ++e) footprint(e, &fp_node[size_t(fp_start[e])]);
+    inc_start.assign(size_t(n_nodes) + 1, 0);
+    for (int64_t k = 0; k < fp_start[n]; ++k) inc_start[fp_node[k] + 1]++;
+    for (int64_t i = 0; i < n_nodes; ++i) inc_start[i + 1] += inc_start[i];
+    inc_elem.resize(size_t(inc_start[n_nodes]));
+    std::vector<int64_t> fill(inc_start.begin(), inc_start.end() - 1);
+    for (int64_t e = 0; e < n; ++e)
+      for (int64_t k = fp_start[e]; k < fp_start[e + 1]; ++k) inc_elem[fill[fp_node[k]]++] = (int32_t)e;
+  }
+
   // --- element colouring: same colour => disjoint footprints
   std::vector<int> ecol(n);
   int n_col = 0;
@@ -292,27 +317,12 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     }
     n_col = nc;
   } else {
-    // node -> elements incidence over footprints
-    std::vector<int64_t> start(n_nodes + 1, 0);
-    std::vector<int32_t> fp(32);
-    for (int64_t e = 0; e < n; ++e) {
-      int k = footprint(e, fp.data());
-      for (int i = 0; i < k; ++i) start[fp[i] + 1]++;
-    }
-    for (int64_t i = 0; i < n_nodes; ++i) start[i + 1] += start[i];
-    std::vector<int32_t> elems(start[n_nodes]);
-    std::vector<int64_t> fill(start.begin(), start.end() - 1);
-    for (int64_t e = 0; e < n; ++e) {
-      int k = footprint(e, fp.data());
-      for (int i = 0; i < k; ++i) elems[fill[fp[i]]++] = (int32_t)e;
-    }
     std::vector<int64_t> mark(256, -1);
     std::fill(ecol.begin(), ecol.end(), -1);
     for (int64_t e = 0; e < n; ++e) {
-      int k = footprint(e, fp.data());
-      for (int i = 0; i < k; ++i)
-        for (int64_t t = start[fp[i]]; t < start[fp[i] + 1]; ++t) {
-          int c = ecol[elems[t]];
+      for (int64_t k = fp_start[e]; k < fp_start[e + 1]; ++k)
+        for (int64_t t = inc_start[fp_node[k]]; t < inc_start[fp_node[k] + 1]; ++t) {
+          int c = ecol[inc_elem[t]];
           if (c >= 0) mark[c] = e;
         }
       int c = 0;
@@ -322,14 +332,16 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
       n_col = std::max(n_col, c + 1);
     }
   }
-  // elements sorted by colour, Morton order within a colour
-  std::vector<int64_t> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return ecol[a] < ecol[b]; });
+  // elements sorted by colour, Morton order within a colour (counting sort)
   m->n_colours = n_col;
   m->colour_start.assign(n_col + 1, 0);
   for (int64_t e = 0; e < n; ++e) m->colour_start[ecol[e] + 1]++;
   for (int c = 0; c < n_col; ++c) m->colour_start[c + 1] += m->colour_start[c];
+  std::vector<int64_t> order(n);
+  {
+    std::vector<int64_t> at(m->colour_start.begin(), m->colour_start.end() - 1);
+    for (int64_t e = 0; e < n; ++e) order[at[ecol[e]]++] = e;
+  }
   std::vector<int32_t> conn_s(size_t(n) * nc);
   std::vector<uint8_t> lev_s(n);
   std::vector<uint32_t> anc_s(size_t(n) * dim);
@@ -353,25 +365,12 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     }
     n_ncol = nc;
   } else {
-    std::vector<int64_t> start(n_nodes + 1, 0);
-    std::vector<int32_t> fp(32);
-    for (int64_t e = 0; e < n; ++e) {
-      int k = footprint(e, fp.data());
-      for (int i = 0; i < k; ++i) start[fp[i] + 1]++;
-    }
-    for (int64_t i = 0; i < n_nodes; ++i) start[i + 1] += start[i];
-    std::vector<int32_t> elems(start[n_nodes]);
-    std::vector<int64_t> fill(start.begin(), start.end() - 1);
-    for (int64_t e = 0; e < n; ++e) {
-      int k = footprint(e, fp.data());
-      for (int i = 0; i < k; ++i) elems[fill[fp[i]]++] = (int32_t)e;
-    }
     std::vector<int64_t> mark(256, -1);
     for (int64_t a = 0; a < n_nodes; ++a) {
-      for (int64_t t = start[a]; t < start[a + 1]; ++t) {
-        int k = footprint(elems[t], fp.data());
-        for (int i = 0; i < k; ++i) {
-          int c = ncol[fp[i]];
+      for (int64_t t = inc_start[a]; t < inc_start[a + 1]; ++t) {
+        const int32_t el = inc_elem[t];
+        for (int64_t k = fp_start[el]; k < fp_start[el + 1]; ++k) {
+          int c = ncol[fp_node[k]];
           if (c >= 0) mark[c] = a;
         }
       }
@@ -382,13 +381,16 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
       n_ncol = std::max(n_ncol, c + 1);
     }
   }
-  std::vector<int32_t> nperm(n_nodes);
-  std::iota(nperm.begin(), nperm.end(), 0);
-  std::stable_sort(nperm.begin(), nperm.end(), [&](int32_t a, int32_t b) { return ncol[a] < ncol[b]; });
   m->n_node_colours = n_ncol;
   m->node_colour_start.assign(n_ncol + 1, 0);
   for (int64_t i = 0; i < n_nodes; ++i) m->node_colour_start[ncol[i] + 1]++;
   for (int c = 0; c < n_ncol; ++c) m->node_colour_start[c + 1] += m->node_colour_start[c];
+  // nodes grouped by colour, increasing index within a colour (counting sort)
+  std::vector<int32_t> nperm(n_nodes);
+  {
+    std::vector<int64_t> at(m->node_colour_start.begin(), m->node_colour_start.end() - 1);
+    for (int64_t i = 0; i < n_nodes; ++i) nperm[at[ncol[i]]++] = (int32_t)i;
+  }
 
   m->n_nodes = n_nodes;
   m->n_hang = n_hang;

@@ -1,0 +1,165 @@
+"""The library's mesh builder on the CPU.
+
+The host code of ``csrc/mesh.cpp`` (validation, node numbering, hanging-node
+constraints, element and node colourings, gather lists) is built with host
+stand-ins for its CUDA runtime calls (``tests/host/cuda_host_stub.cpp``) and
+checked against the oracle mesh: the independent node set, the hanging nodes
+and their parents, the wall nodes; the library's own validation (colours
+with disjoint expanded footprints, exact gather lists) passes on every mesh,
+including remeshed ones; unbalanced and untiled leaf lists are rejected.
+No GPU."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import remesh as R
+from oracle.oracle import OracleMesh
+from paper_1912_12453_gb300 import chns, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1912_12453_gb300", "csrc")
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime.h")):
+            return os.path.join(base, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("g++ or the CUDA headers are missing")
+    out = str(tmp_path_factory.mktemp("meshhost") / "mesh_host")
+    cmd = ["g++", "-O2", "-std=c++17", "-pthread", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", inc,
+           os.path.join(CSRC, "mesh.cpp"), os.path.join(ROOT, "tests", "host", "cuda_host_stub.cpp"),
+           os.path.join(ROOT, "tests", "host", "mesh_host_main.cpp"), "-o", out]
+    subprocess.check_call(cmd)
+    return out
+
+
+def _run(exe, leaves, tmp_path):
+    src, dst = str(tmp_path / "leaves.bin"), str(tmp_path / "mesh.bin")
+    with open(src, "wb") as f:
+        f.write(np.int64(leaves.level.shape[0]).tobytes())
+        f.write(np.int32(leaves.dim).tobytes())
+        f.write(np.int32(leaves.max_level).tobytes())
+        f.write(np.ascontiguousarray(leaves.level, np.uint8).tobytes())
+        f.write(np.ascontiguousarray(leaves.anchor, np.uint32).tobytes())
+    subprocess.check_call([exe, src, dst])
+    raw = open(dst, "rb").read()
+    st, val = np.frombuffer(raw[:8], np.int32)
+    out = {"status": int(st), "validate": int(val)}
+    if st != 0 or val != 0:
+        return out
+    dim, n = leaves.dim, leaves.level.shape[0]
+    q = np.frombuffer(raw[8:], np.int64)
+    n_nodes, n_hang, n_col, origin, n_wall = (int(x) for x in q[:5])
+    k = 5
+    xyz = q[k:k + n_nodes * dim].reshape(n_nodes, dim)
+    k += n_nodes * dim
+    nrec = int(q[k])
+    k += 1
+    rec = q[k:k + nrec].reshape(-1, 5 * dim)
+    k += nrec
+    cs = q[k:k + n_col + 1]
+    hang = {}
+    for r in rec:
+        corner = tuple(int(v) for v in r[:dim])
+        par = [tuple(int(v) for v in r[dim * (b + 1):dim * (b + 2)]) for b in range(4)]
+        hang[corner] = tuple(sorted(p for p in par if p[0] >= 0))
+    out.update(n_nodes=n_nodes, n_hang=n_hang, n_colours=n_col, origin=origin, n_wall=n_wall, xyz=xyz,
+               hang=hang, colour_start=cs, n=n)
+    return out
+
+
+def _oracle_hanging(leaves, om):
+    """corner coordinates -> sorted parent coordinates, from the oracle's P."""
+    start, node, w = om.P()
+    dim = leaves.dim
+    nc = 1 << dim
+    out = {}
+    s = np.int64(1) << (leaves.max_level - leaves.level.astype(np.int64))
+    for e in range(leaves.level.shape[0]):
+        for c in range(nc):
+            r = e * nc + c
+            if start[r + 1] - start[r] <= 1:
+                continue
+            corner = tuple(int(leaves.anchor[e, a]) + (int(s[e]) if (c >> a) & 1 else 0) for a in range(dim))
+            par = tuple(sorted(tuple(int(v) for v in om.coords_int[node[t]]) for t in range(start[r], start[r + 1])))
+            assert set(w[start[r]:start[r + 1]]) <= {0.5, 0.25}
+            out[corner] = par
+    return out
+
+
+def _meshes():
+    cases = [("uniform2d", W.uniform_leaves(2, 4)), ("uniform3d", W.uniform_leaves(3, 3)),
+             ("hang2", W.tiny_leaves(2, "hang")), ("hang3", W.tiny_leaves(3, "hang")),
+             ("band2d", W.band_leaves(2, 3, 7, [W.Sphere((0.45, 0.55), 0.2)], 0.02)),
+             ("band3d", W.band_leaves(3, 2, 5, [W.Sphere((0.45, 0.55, 0.5), 0.2)], 0.03))]
+    for i, wl in enumerate(W.batched_workloads(64)):
+        if wl.leaves.level.shape[0] < 20000:
+            cases.append((f"batched{i}", wl.leaves))
+        if len(cases) >= 8:
+            break
+    return cases
+
+
+@pytest.mark.parametrize("name,leaves", _meshes(), ids=[c[0] for c in _meshes()])
+def test_builder_matches_the_oracle_mesh(exe, tmp_path, name, leaves):
+    got = _run(exe, leaves, tmp_path)
+    assert got["status"] == 0 and got["validate"] == 0, got
+    om = OracleMesh(leaves)
+    assert got["n_nodes"] == om.n_nodes and got["n_hang"] == om.n_hanging
+    assert {tuple(r) for r in got["xyz"].tolist()} == {tuple(r) for r in om.coords_int.tolist()}
+    assert got["hang"] == _oracle_hanging(leaves, om)
+    assert tuple(got["xyz"][got["origin"]]) == (0,) * leaves.dim
+    assert got["n_wall"] == int(om.on_wall.sum())
+    cs = got["colour_start"]
+    assert cs[0] == 0 and cs[-1] == got["n"] and np.all(np.diff(cs) > 0)
+    if len(set(leaves.level.tolist())) == 1:
+        assert got["n_colours"] == 1 << leaves.dim
+
+
+def test_builder_accepts_remeshed_and_adapted_leaves(exe, tmp_path):
+    """Leaf lists produced by the library's remeshing are valid meshes for its
+    builder (balanced, tiled, colourable) and agree with the oracle mesh."""
+    sp0 = [W.Sphere((0.5, 0.35), 0.18)]
+    L = W.band_leaves(2, 3, 7, sp0, 0.02)
+    om = OracleMesh(L)
+    U = np.zeros((om.n_nodes, 5))
+    U[:, 3] = W.phi_profile(om.coords, [W.Sphere((0.5, 0.45), 0.18)], 0.02, True)
+    new, passes = chns.leaves_remesh(L, om.coords_int, U, 3, 7)
+    assert passes >= 1
+    rng = np.random.default_rng(3)
+    adapted = chns.leaves_adapt(new, rng.integers(-1, 2, size=new.n).astype(np.int8))
+    for leaves in (new, adapted):
+        got = _run(exe, leaves, tmp_path)
+        assert got["status"] == 0 and got["validate"] == 0
+        on = OracleMesh(leaves)
+        assert got["n_nodes"] == on.n_nodes and got["n_hang"] == on.n_hanging
+        assert got["hang"] == _oracle_hanging(leaves, on)
+
+
+def test_builder_rejects_unbalanced_and_untiled_leaves(exe, tmp_path):
+    # a level-3 family touching three level-1 leaves at the box centre
+    octs = [(1, (4, 0)), (1, (0, 4)), (1, (4, 4)), (2, (0, 0)), (2, (2, 0)), (2, (0, 2))]
+    octs += [(3, (2 + dx, 2 + dy)) for dx in (0, 1) for dy in (0, 1)]
+    unbal = R._sorted(2, 3, octs)
+    assert _run(exe, unbal, tmp_path)["status"] == 2
+    # the same corner in 3D
+    octs = [(1, (x, y, z)) for x in (0, 4) for y in (0, 4) for z in (0, 4) if (x, y, z) != (0, 0, 0)]
+    octs += [(2, (x, y, z)) for x in (0, 2) for y in (0, 2) for z in (0, 2) if (x, y, z) != (2, 2, 2)]
+    octs += [(3, (2 + dx, 2 + dy, 2 + dz)) for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)]
+    assert _run(exe, R._sorted(3, 3, octs), tmp_path)["status"] == 2
+    # a missing leaf, and leaves out of Morton order
+    U = W.uniform_leaves(2, 2)
+    gap = chns.Leaves(2, 2, U.level[1:], U.anchor[1:])
+    assert _run(exe, gap, tmp_path)["status"] == 2
+    swapped = chns.Leaves(2, 2, U.level, U.anchor[[1, 0] + list(range(2, 16))])
+    assert _run(exe, swapped, tmp_path)["status"] == 2
