@@ -351,3 +351,27 @@ def test_remesh_of_a_settled_mesh_changes_nothing():
     Ua = chns.leaves_transfer(L, om.coords_int, U, oa.coords_int)
     b, passes = chns.leaves_remesh(a, oa.coords_int, Ua, base, top)
     assert passes == 0 and _same(a, b)
+
+
+def test_hand_worked_remesh_library():
+    """The library on the hand-worked case of the oracle pins: phi = x - 0.3
+    on a uniform level-2 quadtree (resolution 2^4), band 0.1, levels 1..3:
+    marks +1 on the columns x < 1/2 and -1 on the others; remeshing gives 32
+    level-3 leaves on the left half and 8 level-2 leaves on the right, in one
+    pass."""
+    U2 = W.uniform_leaves(2, 2)
+    L = chns.Leaves(2, 4, U2.level, U2.anchor.astype(np.uint32) << 2)
+    om = OracleMesh(L)
+    U = np.zeros((om.n_nodes, 5))
+    U[:, 3] = om.coords_int[:, 0] / 16.0 - 0.3
+    mark = chns.leaves_mark_interface(L, om.coords_int, U, L, 1, 3, 0.1)
+    left = L.anchor[:, 0] < 8
+    assert np.all(mark[left] == 1) and np.all(mark[~left] == -1)
+    new, passes = chns.leaves_remesh(L, om.coords_int, U, 1, 3, 0.1)
+    assert passes == 1 and new.n == 40
+    assert np.all(new.level[new.anchor[:, 0] < 8] == 3) and np.all(new.level[new.anchor[:, 0] >= 8] == 2)
+    U[:, 3] -= 0.02   # |phi| = 0.07 at x = 1/4: inside a band of 0.1, outside one of 0.06
+    first = L.anchor[:, 0] < 4
+    assert np.all(chns.leaves_mark_interface(L, om.coords_int, U, L, 1, 3, 0.1)[first] == 1)
+    mark = chns.leaves_mark_interface(L, om.coords_int, U, L, 1, 3, 0.06)
+    assert np.all(mark[first] == -1) and np.all(mark[left & ~first] == 1)
