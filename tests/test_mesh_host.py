@@ -163,3 +163,28 @@ def test_builder_rejects_unbalanced_and_untiled_leaves(exe, tmp_path):
     assert _run(exe, gap, tmp_path)["status"] == 2
     swapped = chns.Leaves(2, 2, U.level, U.anchor[[1, 0] + list(range(2, 16))])
     assert _run(exe, swapped, tmp_path)["status"] == 2
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_builder_on_random_balanced_trees(exe, tmp_path, seed):
+    """Seeded random balanced trees (random split / merge passes from a
+    uniform level, 2D and 3D): the builder's output agrees with the oracle
+    mesh and passes the library's own validation."""
+    rng = np.random.default_rng(2000 + seed)
+    dim = 3 if seed % 3 == 0 else 2
+    top = int(rng.integers(2, 7 if dim == 2 else 5))
+    base = int(rng.integers(1, top + 1))
+    U = W.uniform_leaves(dim, base)
+    cur = chns.Leaves(dim, top, U.level, U.anchor.astype(np.uint32) << (top - base))
+    for _ in range(int(rng.integers(0, 5))):
+        u = rng.uniform(size=cur.n)
+        m = np.where(u < rng.uniform(0, 0.4), 1, np.where(u > 1 - rng.uniform(0, 0.8), -1, 0)).astype(np.int8)
+        cur = chns.leaves_adapt(cur, m)
+        if cur.n > 3000:
+            break
+    got = _run(exe, cur, tmp_path)
+    assert got["status"] == 0 and got["validate"] == 0
+    om = OracleMesh(cur)
+    assert got["n_nodes"] == om.n_nodes and got["n_hang"] == om.n_hanging
+    assert {tuple(r) for r in got["xyz"].tolist()} == {tuple(r) for r in om.coords_int.tolist()}
+    assert got["hang"] == _oracle_hanging(cur, om)

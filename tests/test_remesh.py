@@ -375,3 +375,42 @@ def test_hand_worked_remesh_library():
     assert np.all(chns.leaves_mark_interface(L, om.coords_int, U, L, 1, 3, 0.1)[first] == 1)
     mark = chns.leaves_mark_interface(L, om.coords_int, U, L, 1, 3, 0.06)
     assert np.all(mark[first] == -1) and np.all(mark[left & ~first] == 1)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_trees_match_the_oracle(seed):
+    """Seeded random trees (2D and 3D, root-only to level 6, several
+    adaptation passes with random split / merge rates), then a remesh around
+    a random bubble with random level bounds, and a transfer at random
+    points: the library equals the oracle (leaf lists, pass counts exactly;
+    values to rounding)."""
+    rng = np.random.default_rng(1000 + seed)
+    dim = 3 if seed % 3 == 0 else 2
+    top = int(rng.integers(3, 7 if dim == 2 else 5))
+    base = int(rng.integers(0, top))
+    if base == 0:
+        cur = chns.Leaves(dim, top, [0], [[0] * dim])
+    else:
+        U = W.uniform_leaves(dim, base)
+        cur = chns.Leaves(dim, top, U.level, U.anchor.astype(np.uint32) << (top - base))
+    for _ in range(int(rng.integers(1, 5))):
+        u = rng.uniform(size=cur.n)
+        m = np.where(u < rng.uniform(0, 0.5), 1, np.where(u > 1 - rng.uniform(0, 0.9), -1, 0)).astype(np.int8)
+        lib = chns.leaves_adapt(cur, m)
+        ora = R.adapt(R.OLeaves(dim, top, cur.level, cur.anchor), m)
+        assert _same(lib, ora)
+        cur = lib
+        if cur.n > 2500:
+            break
+    om = OracleMesh(cur)
+    c, r, Cn = rng.uniform(0.2, 0.8, size=dim), rng.uniform(0.1, 0.3), rng.uniform(0.01, 0.08)
+    U = np.zeros((om.n_nodes, dim + 3))
+    U[:, dim + 1] = W.phi_profile(om.coords, [W.Sphere(tuple(c), r)], Cn, bool(seed % 2))
+    lmin = int(rng.integers(0, top))
+    lmax = int(rng.integers(lmin, top + 1))
+    lib, p1 = chns.leaves_remesh(cur, om.coords_int, U, lmin, lmax)
+    ora, p2, margin = R.remesh(R.OLeaves(dim, top, cur.level, cur.anchor), om.coords_int, U, lmin, lmax)
+    if margin > 1e-12:
+        assert _same(lib, ora) and p1 == p2
+    pts = rng.integers(0, (1 << top) + 1, size=(40, dim))
+    assert np.max(np.abs(chns.leaves_transfer(cur, om.coords_int, U, pts) - R.transfer(cur, om.coords_int, U, pts))) < 1e-13
