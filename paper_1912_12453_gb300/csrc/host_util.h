@@ -3,7 +3,9 @@
 // device upload / download of std::vectors.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -76,6 +78,30 @@ class KeyMap {
   std::vector<Slot> slots_;
   size_t mask_ = 0, size_ = 0;
 };
+
+// fn(begin, end) over [0, n) split across host threads; a thread that cannot
+// be started leaves its range to the calling thread
+template <class F>
+inline void parallel_for(int64_t n, int64_t grain, F fn) {
+  const int64_t hw = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), 64));
+  const int nt = int(std::max<int64_t>(1, std::min<int64_t>(hw, (n + grain - 1) / grain)));
+  if (nt <= 1) {
+    fn(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int started = 0;
+  try {
+    for (int t = 1; t < nt; ++t) {
+      th.emplace_back([&fn, n, nt, t] { fn(n * t / nt, n * (t + 1) / nt); });
+      ++started;
+    }
+  } catch (...) {
+  }
+  fn(int64_t(0), n / nt);
+  for (int t = started + 1; t < nt; ++t) fn(n * t / nt, n * (t + 1) / nt);
+  for (auto &x : th) x.join();
+}
 
 inline uint64_t pack(const int64_t *x, int dim) {
   uint64_t k = 0;

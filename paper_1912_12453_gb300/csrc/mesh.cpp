@@ -145,8 +145,11 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     }
     // the parents of the 3^dim - 1 neighbour cells: per axis the cells at
     // a - s, a, a + s inside the box have at most two distinct parents, so
-    // at most 2^dim parents to look up (the leaf's own is always present)
-    for (int64_t e = 0; e < n; ++e) {
+    // at most 2^dim parents to look up (the leaf's own is always present);
+    // leaves checked on host threads, the first unbalanced one reported
+    std::atomic<int64_t> first_bad{n};
+    parallel_for(n, 16384, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1 && e < first_bad.load(std::memory_order_relaxed); ++e) {
       int l = level[e];
       if (l <= 1) continue;
       int64_t s = int64_t(1) << (max_level - l);
@@ -164,15 +167,24 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
         }
         nc3[a] = cnt;
       }
-      for (int i0 = 0; i0 < nc3[0]; ++i0)
-        for (int i1 = 0; i1 < nc3[1]; ++i1)
-          for (int i2 = 0; i2 < nc3[2]; ++i2) {
+      bool ok = true;
+      for (int i0 = 0; i0 < nc3[0] && ok; ++i0)
+        for (int i1 = 0; i1 < nc3[1] && ok; ++i1)
+          for (int i2 = 0; i2 < nc3[2] && ok; ++i2) {
             int64_t x[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
-            if (oct.find(okey(l - 1, x, dim, max_level)) < 0) {
-              set_error("mesh is not 2:1 balanced at leaf %lld", (long long)e);
-              return CHNS_ERR_MESH;
-            }
+            if (oct.find(okey(l - 1, x, dim, max_level)) < 0) ok = false;
           }
+      if (!ok) {
+        int64_t cur = first_bad.load();
+        while (e < cur && !first_bad.compare_exchange_weak(cur, e)) {
+        }
+        break;
+      }
+    }
+    });
+    if (first_bad.load() < n) {
+      set_error("mesh is not 2:1 balanced at leaf %lld", (long long)first_bad.load());
+      return CHNS_ERR_MESH;
     }
   }
 
@@ -291,11 +303,22 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
   std::vector<int64_t> fp_start, inc_start;
   std::vector<int32_t> fp_node, inc_elem;
   if (!uniform) {
-    std::vector<int32_t> fp(32);
     fp_start.assign(size_t(n) + 1, 0);
-    for (int64_t e = 0; e < n; ++e) fp_start[e + 1] = fp_start[e] + footprint(e, fp.data());
+    parallel_for(n, 16384, [&](int64_t e0, int64_t e1) {
+      int32_t fp[32];
+      for (int64_t e = e0; e < e1; ++e) fp_start[e + 1] = footprint(e, fp);
+    });
+    for (int64_t e = 0; e < n; ++e) fp_start[e + 1] += fp_start[e];
     fp_node.resize(size_t(fp_start[n]));
-    for (int64_t e = 0; e < n; ++e) footprint(e, &fp_node[size_t(fp_start[e])]);
+    // through a local buffer: before de-duplication a footprint can hold
+    // more entries than its slot in fp_node
+    parallel_for(n, 16384, [&](int64_t e0, int64_t e1) {
+      int32_t fp[32];
+      for (int64_t e = e0; e < e1; ++e) {
+        const int k = footprint(e, fp);
+        std::copy(fp, fp + k, &fp_node[size_t(fp_start[e])]);
+      }
+    });
     inc_start.assign(size_t(n_nodes) + 1, 0);
     for (int64_t k = 0; k < fp_start[n]; ++k) inc_start[fp_node[k] + 1]++;
     for (int64_t i = 0; i < n_nodes; ++i) inc_start[i + 1] += inc_start[i];

@@ -82,30 +82,6 @@ void children(const Oct &o, int dim, int max_level, std::vector<Oct> &out) {
 
 bool args_ok(int dim, int max_level) { return (dim == 2 || dim == 3) && max_level >= 0 && max_level <= 20; }
 
-// fn(begin, end) over [0, n) split across host threads; a thread that cannot
-// be started leaves its range to the calling thread
-template <class F>
-void parallel_for(int64_t n, int64_t grain, F fn) {
-  const int64_t hw = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), 64));
-  const int nt = int(std::max<int64_t>(1, std::min<int64_t>(hw, (n + grain - 1) / grain)));
-  if (nt <= 1) {
-    fn(int64_t(0), n);
-    return;
-  }
-  std::vector<std::thread> th;
-  int started = 0;
-  try {
-    for (int t = 1; t < nt; ++t) {
-      th.emplace_back([&fn, n, nt, t] { fn(n * t / nt, n * (t + 1) / nt); });
-      ++started;
-    }
-  } catch (...) {
-  }
-  fn(int64_t(0), n / nt);
-  for (int t = started + 1; t < nt; ++t) fn(n * t / nt, n * (t + 1) / nt);
-  for (auto &x : th) x.join();
-}
-
 // Leaves must be aligned to their level, in Morton order and tile the box
 // (the same contract as chns_mesh_create, without the balance requirement).
 chns_status check_tiling(int dim, int max_level, int64_t n, const uint8_t *level, const uint32_t *anchor) {

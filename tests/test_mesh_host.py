@@ -188,3 +188,116 @@ def test_builder_on_random_balanced_trees(exe, tmp_path, seed):
     assert got["n_nodes"] == om.n_nodes and got["n_hang"] == om.n_hanging
     assert {tuple(r) for r in got["xyz"].tolist()} == {tuple(r) for r in om.coords_int.tolist()}
     assert got["hang"] == _oracle_hanging(cur, om)
+
+
+# ---------------------------------------------------------------- AddressSanitizer builds
+
+def _asan_build(tmp_path_factory, name, sources):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("g++ or the CUDA headers are missing")
+    out = str(tmp_path_factory.mktemp("asan") / name)
+    cmd = ["g++", "-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer", "-std=c++17", "-pthread",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", inc] + sources + ["-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no AddressSanitizer runtime: " + r.stderr[-200:])
+    return out
+
+
+@pytest.fixture(scope="module")
+def asan_mesh(tmp_path_factory):
+    return _asan_build(tmp_path_factory, "mesh_host_asan",
+                       [os.path.join(CSRC, "mesh.cpp"), os.path.join(ROOT, "tests", "host", "cuda_host_stub.cpp"),
+                        os.path.join(ROOT, "tests", "host", "mesh_host_main.cpp")])
+
+
+@pytest.fixture(scope="module")
+def asan_octree(tmp_path_factory):
+    return _asan_build(tmp_path_factory, "octree_host_asan",
+                       [os.path.join(CSRC, "mesh.cpp"), os.path.join(CSRC, "octree.cpp"),
+                        os.path.join(ROOT, "tests", "host", "cuda_host_stub.cpp"),
+                        os.path.join(ROOT, "tests", "host", "octree_host_main.cpp")])
+
+
+def _asan_env():
+    env = dict(os.environ)
+    env["ASAN_OPTIONS"] = "detect_leaks=0:abort_on_error=0:exitcode=86"
+    return env
+
+
+def test_mesh_builder_under_address_sanitizer(asan_mesh, tmp_path):
+    """The builder's host code reads and writes only inside its arrays on
+    uniform, banded, batched and random adapted trees, and on rejected ones."""
+    cases = [m for _, m in _meshes()]
+    rng = np.random.default_rng(5)
+    cur = chns.Leaves(3, 5, W.uniform_leaves(3, 2).level, W.uniform_leaves(3, 2).anchor.astype(np.uint32) << 3)
+    for _ in range(3):
+        cur = chns.leaves_adapt(cur, rng.integers(-1, 2, size=cur.n).astype(np.int8))
+    cases.append(cur)
+    octs = [(1, (4, 0)), (1, (0, 4)), (1, (4, 4)), (2, (0, 0)), (2, (2, 0)), (2, (0, 2))]
+    octs += [(3, (2 + dx, 2 + dy)) for dx in (0, 1) for dy in (0, 1)]
+    cases.append(R._sorted(2, 3, octs))
+    for leaves in cases:
+        src, dst = str(tmp_path / "l.bin"), str(tmp_path / "m.bin")
+        with open(src, "wb") as f:
+            f.write(np.int64(leaves.level.shape[0]).tobytes() + np.int32(leaves.dim).tobytes()
+                    + np.int32(leaves.max_level).tobytes() + np.ascontiguousarray(leaves.level, np.uint8).tobytes()
+                    + np.ascontiguousarray(leaves.anchor, np.uint32).tobytes())
+        r = subprocess.run([asan_mesh, src, dst], capture_output=True, text=True, env=_asan_env())
+        assert r.returncode == 0 and "AddressSanitizer" not in r.stderr, r.stderr[-2000:]
+
+
+def _leaf_bytes(leaves):
+    return (np.int64(leaves.level.shape[0]).tobytes() + np.int32(leaves.dim).tobytes()
+            + np.int32(leaves.max_level).tobytes() + np.ascontiguousarray(leaves.level, np.uint8).tobytes()
+            + np.ascontiguousarray(leaves.anchor, np.uint32).tobytes())
+
+
+def test_remeshing_under_address_sanitizer(asan_octree, tmp_path):
+    """The remeshing calls (adapt, remesh, transfer) built with
+    AddressSanitizer stay inside their arrays and give the shared library's
+    results (leaf lists bit for bit, values to rounding)."""
+    src, dst = str(tmp_path / "i.bin"), str(tmp_path / "o.bin")
+
+    def run(mode, payload):
+        with open(src, "wb") as f:
+            f.write(payload)
+        r = subprocess.run([asan_octree, mode, src, dst], capture_output=True, text=True, env=_asan_env())
+        assert r.returncode == 0 and "AddressSanitizer" not in r.stderr, r.stderr[-2000:]
+        return open(dst, "rb").read()
+
+    for dim, base, top in [(2, 3, 7), (3, 2, 5)]:
+        sp = [W.Sphere((0.5, 0.35, 0.5)[:dim], 0.18)]
+        L = W.band_leaves(dim, base, top, sp, 0.02 if dim == 2 else 0.03)
+        om = OracleMesh(L)
+        nf = dim + 3
+        # adapt with random marks
+        mark = np.random.default_rng(dim).integers(-1, 2, size=L.n).astype(np.int8)
+        raw = run("adapt", _leaf_bytes(L) + mark.tobytes())
+        st, m = np.frombuffer(raw[:4], np.int32)[0], int(np.frombuffer(raw[4:12], np.int64)[0])
+        lib = chns.leaves_adapt(L, mark)
+        assert st == 0 and m == lib.n
+        assert np.array_equal(np.frombuffer(raw[12:12 + m], np.uint8), lib.level)
+        assert np.array_equal(np.frombuffer(raw[12 + m:], np.uint32).reshape(-1, dim), lib.anchor)
+        # remesh around a moved bubble
+        U = np.zeros((om.n_nodes, nf))
+        U[:, dim + 1] = W.phi_profile(om.coords, [W.Sphere((0.5, 0.45, 0.5)[:dim], 0.18)], 0.02, True)
+        field = (np.int64(om.n_nodes).tobytes() + np.int32(nf).tobytes()
+                 + np.ascontiguousarray(om.coords_int, np.int64).tobytes() + U.tobytes())
+        raw = run("remesh", _leaf_bytes(L) + field + np.int32(base).tobytes() + np.int32(top).tobytes()
+                  + np.float64(0.9).tobytes())
+        st, m = np.frombuffer(raw[:4], np.int32)[0], int(np.frombuffer(raw[4:12], np.int64)[0])
+        passes = int(np.frombuffer(raw[12:16], np.int32)[0])
+        new, lp = chns.leaves_remesh(L, om.coords_int, U, base, top)
+        assert st == 0 and m == new.n and passes == lp
+        assert np.array_equal(np.frombuffer(raw[16:16 + m], np.uint8), new.level)
+        # transfer to the new mesh's nodes and to the box corners
+        pts = np.concatenate([OracleMesh(new).coords_int, np.zeros((1, dim), np.int64),
+                              np.full((1, dim), 1 << L.max_level, np.int64)])
+        raw = run("transfer", _leaf_bytes(L) + field + np.int64(pts.shape[0]).tobytes()
+                  + np.ascontiguousarray(pts, np.int64).tobytes())
+        assert np.frombuffer(raw[:4], np.int32)[0] == 0
+        got = np.frombuffer(raw[4:], np.float64).reshape(-1, nf)
+        # (the two builds may contract multiply-adds differently)
+        assert np.max(np.abs(got - chns.leaves_transfer(L, om.coords_int, U, pts))) <= 1e-14
