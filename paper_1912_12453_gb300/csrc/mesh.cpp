@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "chns_internal.h"
 #include "host_util.h"
@@ -188,22 +189,61 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
     }
   }
 
-  // --- nodes: unique corners in first-appearance order
-  KeyMap nodes(size_t(n) * (dim == 2 ? 2 : 3) + 64);
+  // --- nodes: unique corners in first-appearance order.  The corner keys are
+  // split into shards by a hash; each shard's map is filled by one thread
+  // scanning all corners in order, so it keeps every key's first corner; the
+  // node ids then follow the first corners in corner order.
+  const int64_t n_slots = n * nc;
+  std::vector<uint64_t> ckey(static_cast<size_t>(n_slots));
+  parallel_for(n, 16384, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int64_t s = int64_t(1) << (max_level - level[e]);
+      for (int c = 0; c < nc; ++c) {
+        int64_t x[3];
+        for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a] + (((c >> a) & 1) ? s : 0);
+        ckey[e * nc + c] = pack(x, dim);
+      }
+    }
+  });
+  const int n_shards = int(std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>(std::thread::hardware_concurrency(), 64), n_slots / 65536 + 1)));
+  auto shard_of = [n_shards](uint64_t k) {
+    k ^= k >> 31;
+    k *= 0x7fb5d329728ea185ull;
+    k ^= k >> 27;
+    return int((k >> 32) % uint64_t(n_shards));
+  };
+  std::vector<KeyMap> shard;
+  shard.reserve(n_shards);
+  for (int t = 0; t < n_shards; ++t) shard.emplace_back(size_t(n) * (dim == 2 ? 2 : 3) / n_shards + 64);
+  parallel_for(n_shards, 1, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t)
+      for (int64_t k = 0; k < n_slots; ++k)
+        if (shard_of(ckey[k]) == t) shard[t].insert(ckey[k], k);
+  });
+  std::vector<int32_t> first(static_cast<size_t>(n_slots));
+  parallel_for(n_slots, 65536, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) first[k] = (int32_t)shard[shard_of(ckey[k])].find(ckey[k]);
+  });
   std::vector<int64_t> all_xyz;
-  std::vector<int32_t> corner_all(size_t(n) * nc);
+  std::vector<int32_t> corner_all(static_cast<size_t>(n_slots));
   all_xyz.reserve(size_t(n) * (dim == 2 ? 2 : 3) * dim);
-  for (int64_t e = 0; e < n; ++e) {
-    int64_t s = int64_t(1) << (max_level - level[e]);
-    for (int c = 0; c < nc; ++c) {
-      int64_t x[3];
-      for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a] + (((c >> a) & 1) ? s : 0);
-      auto r = nodes.insert(pack(x, dim), (int64_t)(all_xyz.size() / dim));
-      if (r.second)
-        for (int a = 0; a < dim; ++a) all_xyz.push_back(x[a]);
-      corner_all[e * nc + c] = (int32_t)r.first;
+  for (int64_t k = 0; k < n_slots; ++k) {
+    if (first[k] == k) {
+      corner_all[k] = (int32_t)(all_xyz.size() / dim);
+      const int64_t e = k / nc;
+      const int c = int(k % nc);
+      const int64_t s = int64_t(1) << (max_level - level[e]);
+      for (int a = 0; a < dim; ++a) all_xyz.push_back(anchor[e * dim + a] + (((c >> a) & 1) ? s : 0));
+    } else {
+      corner_all[k] = corner_all[first[k]];
     }
   }
+  // node id of a point key, -1 if no leaf has a corner there
+  auto node_find = [&](uint64_t key) -> int64_t {
+    const int64_t f = shard[shard_of(key)].find(key);
+    return f < 0 ? -1 : corner_all[f];
+  };
   const int64_t n_all = (int64_t)(all_xyz.size() / dim);
 
   // --- hanging nodes: a node at the midpoint of an edge, or the centre of a
@@ -220,7 +260,7 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
       if (nhalf == 0 || nhalf == dim) continue;
       int64_t x[3];
       for (int a = 0; a < dim; ++a) x[a] = anchor[e * dim + a] + ch[a] * (s / 2);
-      int64_t id = nodes.find(pack(x, dim));
+      int64_t id = node_find(pack(x, dim));
       if (id < 0) continue;
       int32_t par[4] = {-1, -1, -1, -1};
       for (int b = 0; b < (1 << nhalf); ++b) {
@@ -230,7 +270,7 @@ chns_status build_mesh(int dim, int64_t n, const uint8_t *level, const uint32_t 
           if (ch[a] == 1) y[a] = anchor[e * dim + a] + (((b >> bit++) & 1) ? s : 0);
           else y[a] = anchor[e * dim + a] + (ch[a] == 2 ? s : 0);
         }
-        int64_t pid = nodes.find(pack(y, dim));
+        int64_t pid = node_find(pack(y, dim));
         if (pid < 0) { set_error("hanging node parent missing (mesh not conforming)"); return CHNS_ERR_MESH; }
         par[b] = (int32_t)pid;
       }
